@@ -1,0 +1,230 @@
+"""Plain FP64 CPU oracle of the free-boundary exact-exchange (EXX) operator.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call or
+execute this module: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it.  It shares
+no code with the CUDA path (``paper_1712_07973_gb300``), and it does not import
+that package.
+
+What it computes (arXiv 1712.07973, Ratcliff et al.):
+
+* Sec. 2, Eq. 1 defines the one-body density matrix with occupations f_i; for
+  real orbitals the co-density of a pair is rho_ij = psi_i * psi_j (Sec. 2.1,
+  "Kernel 1"), and rho_ij = rho_ji.
+* Sec. 2, the equation after Eq. daction: V_ij solves the Poisson equation
+  lap V_ij = -4 pi rho_ij, i.e. V_ij = rho_ij convolved with 1/|r - r'|.
+  Sec. 2.1.2 states that this convolution is done exactly, with appropriate
+  zero padding, by Fourier techniques, with a Green's function discretised on
+  the uniform mesh for free boundary conditions.
+* Sec. 2, Eq. HF and the E_X equation that follows the pair-count paragraph:
+  E_x = -(alpha/2) * sum_{i,j} f_i f_j  int rho_ij V_ij.  The factor alpha is
+  the exact-exchange fraction of the hybrid (PBE0: 1/4, Sec. 3).
+* Sec. 2, Eq. daction: (Vx psi)_i = -alpha * sum_j f_j V_ij psi_j.
+* Sec. 2, pair-count paragraph: all N(N+1)/2 co-densities are formed; the
+  symmetry V_ij = V_ji lets pair (i, j) serve both (Vx psi)_i and (Vx psi)_j
+  (Sec. 2.1, round-robin paragraph).
+
+Readings where the paper is silent (each is also listed in the design doc):
+
+* The paper names the interpolating-scaling-function Green's function but
+  prints no formula for it.  This oracle uses the band-limited ("sinc basis")
+  free-space kernel: G[m] = h^3 * G_BL(m h) with
+  G_BL(r) = (2 pi)^-3 * int over the cube |k_d| <= pi/h of (4 pi / k^2) e^{i k.r} d^3k,
+  which is the exact Coulomb potential of any density band-limited to the
+  grid's Brillouin zone.  The point-sampled Hockney kernel (G[m] = h^3/|m h|,
+  G[0] = h^2 times the cell average of 1/r) is offered as a second option.
+* Grid nodes sit at x_m = m h, m = 0..n-1, per axis; arrays are indexed
+  [z, y, x] with x fastest.
+* Occupations are used exactly as passed (no sum over spin channels).
+* E_ij = h^3 * sum_m rho_ij[m] V_ij[m] (rectangle-rule quadrature on the mesh).
+
+Precision: FP64 throughout.
+"""
+
+import math
+
+import numpy as np
+from scipy import fft as sfft
+from scipy import special as sspecial
+from scipy import integrate as sint
+
+__all__ = [
+    "KERNEL_SINC",
+    "KERNEL_HOCKNEY",
+    "sinc_kernel_g1d",
+    "kernel_real_space",
+    "kernel_spectrum",
+    "poisson",
+    "direct_sum_potential",
+    "pair_list",
+    "exx",
+    "exx_pair",
+    "exx_energy_gradient",
+]
+
+KERNEL_SINC = "sinc"
+KERNEL_HOCKNEY = "hockney"
+
+# --------------------------------------------------------------------------
+# Free-boundary Green's function on the mesh (Sec. 2.1.2; reading above)
+# --------------------------------------------------------------------------
+#
+# With 1/r = (2/sqrt(pi)) int_0^inf exp(-t^2 r^2) dt and the Fourier pair of a
+# Gaussian, the band-limited kernel separates per axis:
+#     G_BL(r) = (2/sqrt(pi)) int_0^inf  prod_{d=x,y,z} g(t, r_d)  dt,
+#     g(t, x) = (1/2pi) int_{-pi/h}^{pi/h} (sqrt(pi)/t) exp(-k^2/(4t^2)) cos(kx) dk.
+# For h = 1 and integer x = m this 1D factor has the closed form
+#     g(t, m) = exp(-t^2 m^2) - (-1)^m exp(-pi^2/(4t^2)) Re w(-t m + i pi/(2t)),
+# with w the Faddeeva function (w(z) = exp(-z^2) erfc(-iz)), and g(t, 0) =
+# erf(pi/(2t)).  Scaling: G[m] = h^3 G_BL(m h; h) = h^2 G_BL(m; 1).
+
+# t-integral: trapezoid rule in s = ln t.  The integrand t * prod g is analytic
+# in the strip |Im s| < pi/4 and decays like e^{s} (s -> -inf) and e^{-2s}
+# (s -> +inf), so the rule converges geometrically with the step.
+_S_MIN, _S_MAX, _S_STEP = -40.0, 20.0, 0.1
+
+
+def sinc_kernel_g1d(t, m):
+    """1D factor g(t, m) of the band-limited kernel for h = 1 (closed form)."""
+    t = np.asarray(t, dtype=np.float64)[:, None]
+    m = np.asarray(m, dtype=np.float64)[None, :]
+    a = np.pi / (2.0 * t)
+    z = -t * m + 1j * a
+    sign = np.where(np.mod(m, 2.0) == 0.0, 1.0, -1.0)
+    out = np.exp(-(t * m) ** 2) - sign * np.exp(-a * a) * np.real(sspecial.wofz(z))
+    # m = 0: g = erf(pi/(2t)) evaluated directly (the form above cancels there).
+    zero = (m == 0.0)[0]
+    if np.any(zero):
+        out[:, zero] = sspecial.erf(a[:, 0])[:, None]
+    return out
+
+
+def _sinc_kernel_octant(n):
+    """G_BL(m; h=1) for m in [0, n]^3 (octant; G is even per axis)."""
+    s = np.arange(_S_MIN, _S_MAX + 0.5 * _S_STEP, _S_STEP)
+    t = np.exp(s)
+    w = _S_STEP * t * (2.0 / math.sqrt(math.pi))
+    w[0] *= 0.5
+    w[-1] *= 0.5
+    m = np.arange(n + 1)
+    g = sinc_kernel_g1d(t, m)  # (nt, n+1)
+    nt = t.size
+    # G[a, b, c] = sum_t w_t g[t,a] g[t,b] g[t,c]   (a plain contraction)
+    gw = g * w[:, None]
+    ab = (gw[:, :, None] * g[:, None, :]).reshape(nt, -1)  # (nt, (n+1)^2)
+    G = (ab.T @ g).reshape(n + 1, n + 1, n + 1)
+    # tail t > e^{S_MAX}: only m = 0 is not negligible; prod g ~ pi^{3/2} t^-3
+    # there, so (2/sqrt(pi)) int_T^inf pi^{3/2} t^-3 dt = pi / T^2.
+    G[0, 0, 0] += math.pi * math.exp(-2.0 * _S_MAX)
+    return G
+
+
+def _hockney_cell_average():
+    """Average of 1/r over the unit cube centred at the origin.
+
+    Splitting the cube into the 24 pyramids where one |coordinate| is largest
+    and scaling the two others by it gives 3 * int_0^1 asinh(1/sqrt(1+a^2)) da.
+    """
+    val, _ = sint.quad(lambda a: np.arcsinh(1.0 / np.sqrt(1.0 + a * a)), 0.0, 1.0,
+                       epsabs=1e-14, epsrel=1e-14, limit=200)
+    return 3.0 * val
+
+
+def kernel_real_space(n, h, kind=KERNEL_SINC):
+    """Real-space mesh kernel G[m] for m in [0, n]^3, including the h^3 weight.
+
+    V[m] = sum_{m'} G[|m - m'|] rho[m'] (absolute difference per axis) is the
+    discrete free-boundary potential of the co-density rho.
+    """
+    if kind == KERNEL_SINC:
+        return (h * h) * _sinc_kernel_octant(n)
+    if kind == KERNEL_HOCKNEY:
+        m = np.arange(n + 1, dtype=np.float64)
+        r = np.sqrt(m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2)
+        with np.errstate(divide="ignore"):
+            G = 1.0 / r
+        G[0, 0, 0] = _hockney_cell_average()
+        return (h * h) * G
+    raise ValueError(f"unknown kernel kind {kind!r}")
+
+
+def kernel_spectrum(G):
+    """Spectrum of the zero-padded (2n)^3 periodic embedding of G.
+
+    G~[d mod 2n] = G[|d|] for d in [-(n-1), n]; the slot d = n is never used by
+    outputs in [0, n) and carries G[n] so that G~ stays even and its DFT real.
+    Returns the real half spectrum of shape (2n, 2n, n+1) in scipy's rfftn
+    layout (last axis = x, k_x in [0, n]).
+    """
+    n = G.shape[0] - 1
+    idx = np.concatenate([np.arange(n + 1), np.arange(n - 1, 0, -1)])
+    Gt = G[np.ix_(idx, idx, idx)]
+    Ghat = sfft.rfftn(Gt, workers=-1)
+    return np.ascontiguousarray(Ghat.real)
+
+
+def poisson(rho, Ghat):
+    """V = G * rho (aperiodic) through the zero-padded 2n FFT (Sec. 2.1.2)."""
+    n = rho.shape[0]
+    pad = np.zeros((2 * n,) * 3, dtype=np.float64)
+    pad[:n, :n, :n] = rho
+    V = sfft.irfftn(sfft.rfftn(pad, workers=-1) * Ghat, s=(2 * n,) * 3, workers=-1)
+    return np.ascontiguousarray(V[:n, :n, :n])
+
+
+def direct_sum_potential(rho, G):
+    """Brute force V[m] = sum_{m'} G[|m-m'|] rho[m'] (O(n^6); tiny grids only)."""
+    n = rho.shape[0]
+    idx = np.arange(n)
+    dif = np.abs(idx[:, None] - idx[None, :])  # (m, m')
+    V = np.empty_like(rho)
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                V[z, y, x] = np.sum(G[dif[z][:, None, None], dif[y][None, :, None],
+                                      dif[x][None, None, :]] * rho)
+    return V
+
+
+def pair_list(N):
+    """All N(N+1)/2 pairs (i, j), i <= j (Sec. 2, pair-count paragraph)."""
+    return [(i, j) for i in range(N) for j in range(i, N)]
+
+
+def exx_pair(psi_i, psi_j, Ghat, h):
+    """One pair: co-density, potential and E_ij = h^3 sum rho_ij V_ij."""
+    rho = psi_i * psi_j
+    V = poisson(rho, Ghat)
+    return V, (h ** 3) * float(np.sum(rho * V))
+
+
+def exx(psi, occ, alpha, h, Ghat, want_vx=True):
+    """Exact exchange of real orbitals psi[N, n, n, n] (FP64).
+
+    Returns (E_x, Vxpsi or None, Eij) with
+      E_x      = -(alpha/2) sum_{i,j} f_i f_j E_ij,
+      Vxpsi[i] = -alpha sum_j f_j V_ij psi_j,
+      Eij      = symmetric matrix of h^3 sum rho_ij V_ij.
+    Pair (i, j), i < j, feeds both i and j; i = j feeds i once.
+    """
+    psi = np.asarray(psi, dtype=np.float64)
+    occ = np.asarray(occ, dtype=np.float64)
+    N = psi.shape[0]
+    Eij = np.zeros((N, N))
+    vx = np.zeros_like(psi) if want_vx else None
+    for i, j in pair_list(N):
+        V, e = exx_pair(psi[i], psi[j], Ghat, h)
+        Eij[i, j] = Eij[j, i] = e
+        if want_vx:
+            vx[i] += (-alpha * occ[j]) * V * psi[j]
+            if i != j:
+                vx[j] += (-alpha * occ[i]) * V * psi[i]
+    Ex = -0.5 * alpha * float(occ @ Eij @ occ)
+    return Ex, vx, Eij
+
+
+def exx_energy_gradient(psi, occ, alpha, h, Ghat):
+    """E_x and dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k (Eq. daction from delta E/delta F)."""
+    Ex, vx, _ = exx(psi, occ, alpha, h, Ghat, want_vx=True)
+    grad = 2.0 * (h ** 3) * np.asarray(occ)[:, None, None, None] * vx
+    return Ex, grad

@@ -1,0 +1,127 @@
+"""Seeded synthetic Kohn-Sham-like orbitals on a uniform cubic mesh.
+
+This module only manufactures inputs.  It holds none of the exact-exchange
+arithmetic, so both the FP64 oracle's tests and the CUDA path can consume the
+same arrays.  Everything is FP64 NumPy, driven by ``numpy.random.default_rng``
+so that the same seed gives the same orbitals on every machine (up to the last
+bits of the LAPACK eigensolver used by the Lowdin step).
+
+Recipe (stands in for the pseudopotential orbitals of the paper's H2O / UO2
+runs, Sec. 3, whose structures and grids are not published):
+
+* grid nodes at x_m = m h, m = 0..n-1 per axis, arrays indexed [z, y, x];
+* "atom" sites uniform in the central 60% of the box, or on a jittered cubic
+  lattice (the large cluster workload);
+* each orbital is a sum of Gaussians exp(-|r-R|^2 / (2 sigma^2)) centred on
+  random sites, of type s, or x/y/z times the Gaussian (p type), with
+  N(0,1) coefficients and sigma uniform in a given range;
+* the set is Lowdin-orthonormalised with the discrete inner product
+  S_ij = h^3 sum_m phi_i phi_j, psi = S^{-1/2} phi.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = ["OrbitalRecipe", "make_orbitals", "workload", "WORKLOADS", "batched_workload"]
+
+
+@dataclass
+class OrbitalRecipe:
+    n: int                       # grid points per axis
+    h: float                     # grid spacing (bohr)
+    norb: int                    # number of orbitals
+    nsites: int                  # number of atom sites
+    seed: int
+    gauss_per_orb: int = 3
+    sigma: tuple = (0.8, 1.5)
+    p_type: bool = False         # include x/y/z * Gaussian terms
+    lattice: float = 0.0         # >0: sites on a jittered cubic lattice (bohr)
+    occupation: float = 2.0
+    alpha: float = 0.25
+    extra: dict = field(default_factory=dict)
+
+
+def _sites(rng, r: OrbitalRecipe):
+    L = (r.n - 1) * r.h
+    if r.lattice > 0.0:
+        a = r.lattice
+        c = 0.5 * L
+        k = int(np.ceil(np.cbrt(r.nsites))) + 3
+        g = np.arange(-k, k + 1, dtype=np.float64)
+        P = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+        d2 = np.sum(P * P, axis=1)
+        # nearest to the centre; ties broken by lexicographic index (stable sort)
+        order = np.argsort(d2, kind="stable")[: r.nsites]
+        P = c + a * P[order]
+        P = P + rng.uniform(-0.1 * a, 0.1 * a, size=P.shape)
+        return P
+    return rng.uniform(0.2 * L, 0.8 * L, size=(r.nsites, 3))
+
+
+def make_orbitals(r: OrbitalRecipe, dtype=np.float64):
+    """Return psi[norb, n, n, n] (Lowdin-orthonormal, FP64 unless dtype given)."""
+    rng = np.random.default_rng(r.seed)
+    sites = _sites(rng, r)
+    x = np.arange(r.n, dtype=np.float64) * r.h
+    phi = np.zeros((r.norb, r.n, r.n, r.n), dtype=np.float64)
+    for o in range(r.norb):
+        at = rng.integers(0, r.nsites, size=r.gauss_per_orb)
+        sig = rng.uniform(r.sigma[0], r.sigma[1], size=r.gauss_per_orb)
+        coef = rng.standard_normal(r.gauss_per_orb)
+        typ = rng.integers(0, 4, size=r.gauss_per_orb) if r.p_type else np.zeros(r.gauss_per_orb, int)
+        for g in range(r.gauss_per_orb):
+            R = sites[at[g]]
+            s2 = 2.0 * sig[g] ** 2
+            dz, dy, dx = x - R[2], x - R[1], x - R[0]
+            gz, gy, gx = np.exp(-dz * dz / s2), np.exp(-dy * dy / s2), np.exp(-dx * dx / s2)
+            if typ[g] == 1:
+                gx = gx * dx
+            elif typ[g] == 2:
+                gy = gy * dy
+            elif typ[g] == 3:
+                gz = gz * dz
+            phi[o] += coef[g] * (gz[:, None, None] * gy[None, :, None] * gx[None, None, :])
+    flat = phi.reshape(r.norb, -1)
+    S = (r.h ** 3) * (flat @ flat.T)
+    w, U = np.linalg.eigh(S)
+    Sm12 = (U / np.sqrt(w)) @ U.T
+    psi = (Sm12 @ flat).reshape(phi.shape)
+    return np.ascontiguousarray(psi.astype(dtype, copy=False))
+
+
+# Workloads: the five configurations the benchmarks and parity tests use.
+WORKLOADS = {
+    # plain FP64: 4 orbitals, 32^3 grid (64^3 padded), 3 s-Gaussians each
+    "c1_fp64_n32_N4": OrbitalRecipe(n=32, h=0.4, norb=4, nsites=4, seed=0,
+                                    gauss_per_orb=3, sigma=(0.8, 1.5)),
+    # FP32 forward: 64 orbitals, 96^3 (192^3 padded), 16 s/p Gaussians each
+    "c2_fp32_n96_N64": OrbitalRecipe(n=96, h=0.4, norb=64, nsites=32, seed=1,
+                                     gauss_per_orb=16, sigma=(0.7, 1.8), p_type=True),
+    # autograd: 128 orbitals, 128^3 (256^3 padded)
+    "c3_grad_n128_N128": OrbitalRecipe(n=128, h=0.37, norb=128, nsites=64, seed=2,
+                                       gauss_per_orb=16, sigma=(0.7, 1.8), p_type=True),
+    # large cluster: 512 orbitals, 160^3 (320^3 padded), jittered 0.35 nm lattice
+    "c5_large_n160_N512": OrbitalRecipe(n=160, h=0.42, norb=512, nsites=256, seed=4,
+                                        gauss_per_orb=16, sigma=(0.7, 1.8), p_type=True,
+                                        lattice=6.614),
+}
+
+
+def workload(name, dtype=np.float64):
+    r = WORKLOADS[name]
+    return r, make_orbitals(r, dtype=dtype)
+
+
+def batched_workload(seed=3, nmol=16, grids=(48, 64, 80, 96, 112, 128), nrange=(8, 96)):
+    """Recipes of the batched, uneven workload: nmol molecules, N_m ~ U{8..96},
+    n_m drawn from ``grids``, h = 0.4, sites proportional to N_m / 2."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for mol in range(nmol):
+        N = int(rng.integers(nrange[0], nrange[1] + 1))
+        n = int(grids[int(rng.integers(0, len(grids)))])
+        out.append(OrbitalRecipe(n=n, h=0.4, norb=N, nsites=max(2, N // 2),
+                                 seed=int(rng.integers(0, 2 ** 31 - 1)),
+                                 gauss_per_orb=16, sigma=(0.7, 1.8), p_type=True))
+    return out
