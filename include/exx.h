@@ -1,0 +1,164 @@
+/*
+ * exx.h -- C ABI of the GB300 (sm_103a) exact-exchange operator.
+ *
+ * The library applies the exact-exchange (Fock) operator of hybrid density
+ * functionals to N real orbitals sampled on a uniform cubic grid with free
+ * (isolated) boundary conditions, following arXiv 1712.07973 (Ratcliff et al.):
+ *
+ *   rho_ij(r)  = psi_i(r) psi_j(r)                       (Sec. 2.1, kernel 1)
+ *   V_ij       = G * rho_ij, the free-BC Poisson solution (Sec. 2.1.2, kernel 2;
+ *                exact aperiodic convolution through a zero-padded 2n FFT)
+ *   E_x        = -(alpha/2) sum_{i,j} f_i f_j h^3 sum_r rho_ij V_ij
+ *                                                        (Sec. 2, Eq. HF and the
+ *                                                         E_X equation after the
+ *                                                         pair-count paragraph)
+ *   (Vx psi)_i = -alpha sum_j f_j V_ij psi_j             (Sec. 2, Eq. daction)
+ *
+ * over all N(N+1)/2 pairs i <= j (Sec. 2, pair-count paragraph; Table
+ * pscount), each pair feeding both i and j (Sec. 2.1, round-robin paragraph).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Orbital arrays are row-major [norb][n][n][n] with x fastest (index
+ *   ((o*n + z)*n + y)*n + x), grid nodes at x_m = m*h, m = 0..n-1.
+ * - "device" pointers are CUDA device (or managed) memory on the current
+ *   device; "host" pointers are ordinary host memory.  The caller keeps
+ *   ownership of every pointer it passes; the plan owns only what it allocates.
+ * - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued on that stream.
+ * - Every entry point returns an exx_status_t and never aborts the process.
+ *   On EXX_ERR_CUDA the CUDA error string is kept in the plan and returned by
+ *   exx_last_error().
+ * - A plan is not thread-safe: calls on one plan must not overlap in time
+ *   (they share the plan's workspace).  Different plans are independent.
+ */
+#ifndef EXX_GB300_H
+#define EXX_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct exx_plan_s* exx_plan_t;
+
+typedef enum {
+  EXX_OK = 0,
+  EXX_ERR_INVALID_ARG = 1,   /* NULL pointer, n < 2, h <= 0, norb < 1, bad enum */
+  EXX_ERR_CUDA = 2,          /* a CUDA runtime call failed (see exx_last_error)  */
+  EXX_ERR_OOM = 3,           /* device workspace could not be allocated          */
+  EXX_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up               */
+  EXX_ERR_NOT_SUPPORTED = 5  /* non-cubic grid, 2n with a prime factor > 7, or a
+                                size beyond the compiled kernels                  */
+} exx_status_t;
+
+typedef enum {
+  EXX_FP64 = 0,  /* FFTs, products and reductions in FP64; psi/vxpsi are double  */
+  EXX_FP32 = 1   /* FFTs and products in FP32, kernel built in FP64, E_x and the
+                    Vx psi accumulation across pairs in FP64; psi is float        */
+} exx_precision_t;
+
+typedef enum {
+  EXX_KERNEL_SINC = 0,    /* band-limited free-space kernel (default): exact for
+                             densities band-limited to the grid's Brillouin zone */
+  EXX_KERNEL_HOCKNEY = 1  /* point-sampled h^3/|r|, cell-averaged origin; O(h^2)  */
+} exx_kernel_t;
+
+/* Plan flags (bitwise or). */
+#define EXX_FLAG_VX_FP64 1u  /* FP32 plans: write vxpsi as double instead of float */
+
+/*
+ * exx_plan_create -- build a plan for fixed (grid, h, alpha, occupations).
+ *   out          host, receives the plan handle (set to NULL on failure).
+ *   grid[3]      host, points per axis (nx, ny, nz); must be equal (cubic),
+ *                2 <= n, and 2n = 2^a 3^b 5^c 7^d within the compiled sizes.
+ *   h[3]         host, grid spacing per axis in bohr; must be equal and > 0.
+ *   alpha        exact-exchange fraction (PBE0: 0.25, Sec. 3).
+ *   occupations  host, norb values f_i (Eq. 1); copied into the plan.
+ *   norb         number of orbitals N >= 1.
+ *   precision    exx_precision_t.
+ *   kernel       exx_kernel_t.
+ *   flags        EXX_FLAG_* bits.
+ *   cuda_stream  stream for the plan's set-up uploads (synchronised on return).
+ * The FP64 kernel spectrum is built on the host (Sec. 2.1.2 reading: the
+ * Green's function discretised on the mesh), uploaded once, and workspaces for
+ * one pair tile are allocated with cudaMalloc.
+ */
+exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[3],
+                             double alpha, const double* occupations, int norb,
+                             int precision, int kernel, unsigned flags, void* cuda_stream);
+
+/*
+ * exx_energy -- E_x only (forward transforms and the Parseval sum; no inverse).
+ *   psi    device, [norb][n][n][n], double (EXX_FP64) or float (EXX_FP32).
+ *   E_out  host, receives E_x in hartree.  The call synchronises the stream.
+ */
+exx_status_t exx_energy(exx_plan_t plan, const void* psi, double* E_out, void* cuda_stream);
+
+/*
+ * exx_apply -- E_x and the exchange action vxpsi = (Vx psi)_i for all i.
+ *   psi    device, as for exx_energy.
+ *   vxpsi  device, [norb][n][n][n]; double for EXX_FP64 or with
+ *          EXX_FLAG_VX_FP64, else float.  Overwritten (not accumulated).
+ *   E_out  host, may be NULL.  If non-NULL the call synchronises the stream.
+ * The gradient of E_x is dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k.
+ */
+exx_status_t exx_apply(exx_plan_t plan, const void* psi, void* vxpsi, double* E_out,
+                       void* cuda_stream);
+
+/*
+ * exx_apply_async -- as exx_apply, but E_x is written to device memory and the
+ * call never synchronises (E_dev: device, one double; may be NULL).
+ */
+exx_status_t exx_apply_async(exx_plan_t plan, const void* psi, void* vxpsi, double* E_dev,
+                             void* cuda_stream);
+
+/*
+ * exx_energy_async -- as exx_energy with E_x written to device memory; no sync.
+ */
+exx_status_t exx_energy_async(exx_plan_t plan, const void* psi, double* E_dev,
+                              void* cuda_stream);
+
+/*
+ * exx_pair_energies -- per-pair energies E_ij = h^3 sum_r rho_ij V_ij of the
+ * last exx_energy/exx_apply call on this plan, copied to host memory in the
+ * order (0,0),(0,1)..(0,N-1),(1,1),..,(N-1,N-1): N(N+1)/2 doubles.  Synchronises
+ * the stream.
+ */
+exx_status_t exx_pair_energies(exx_plan_t plan, double* out_host, void* cuda_stream);
+
+/*
+ * exx_plan_info -- sizes chosen by the plan (host out-parameters, each may be
+ * NULL): tile edge (orbitals per tile side), number of pair tiles, device
+ * workspace bytes, number of kernel launches one exx_apply enqueues.
+ */
+exx_status_t exx_plan_info(exx_plan_t plan, int* tile, int* ntiles, size_t* workspace_bytes,
+                           int* launches_apply, int* launches_energy);
+
+/* exx_plan_destroy -- free the plan and its device memory (NULL is a no-op). */
+exx_status_t exx_plan_destroy(exx_plan_t plan);
+
+/*
+ * exx_kernel_spectrum -- host-only: the FP64 spectrum of the zero-padded mesh
+ * kernel, Ghat[k] = sum_d G~[d] exp(-i pi k.d / n) for k in [0, n]^3 (one
+ * octant; Ghat is real and even per axis), unscaled.  out_host holds (n+1)^3
+ * doubles, index (kz*(n+1) + ky)*(n+1) + kx.  Needs no GPU.
+ */
+exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double* out_host);
+
+/* exx_status_string -- static text for a status code. */
+const char* exx_status_string(exx_status_t status);
+
+/* exx_last_error -- text of the last CUDA failure seen by this plan (or ""). */
+const char* exx_last_error(exx_plan_t plan);
+
+/* exx_version -- library version string. */
+const char* exx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXX_GB300_H */

@@ -1,0 +1,444 @@
+// C ABI of the exact-exchange operator (declared in include/exx.h).
+//
+// A plan holds the FP64-built kernel spectrum (Sec. 2.1.2 of arXiv
+// 1712.07973: Green's function on the mesh, applied by a zero-padded FFT),
+// the FFT twiddles, the pair-tile schedule over the N(N+1)/2 pairs (Sec. 2,
+// pair-count paragraph; Table pscount) and the device workspace of one tile.
+// exx_apply / exx_energy enqueue the tile pipeline on the caller's stream:
+//   fwd_xy -> zconv -> pair_energy [-> inv_yx -> accum]   per pair tile
+//   exx_total [-> convert]                                once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/exx.h"
+#include "exx_ops.cuh"
+
+namespace exx_host {
+bool kernel_spectrum_octant(int n, double h, int kind, double* out);
+}
+
+namespace exx {
+
+// ---------------------------------------------------------------- registry
+#define EXX_SIZES(X)                                                                         \
+  X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(16) X(18) X(20) X(24) X(28)    \
+  X(32) X(36) X(40) X(48) X(56) X(64) X(72) X(80) X(96) X(112) X(128)
+
+#define EXX_DECL(N) const Ops* ops_f32_##N(); const Ops* ops_f64_##N();
+EXX_SIZES(EXX_DECL)
+#undef EXX_DECL
+
+static const Ops* lookup_ops(int prec, int n) {
+  switch (n) {
+#define EXX_CASE(N) \
+  case N:           \
+    return prec == EXX_FP64 ? ops_f64_##N() : ops_f32_##N();
+    EXX_SIZES(EXX_CASE)
+#undef EXX_CASE
+    default:
+      return nullptr;
+  }
+}
+
+// ------------------------------------------------------ pair enumeration
+// Global pair id of (i, j), i <= j, in row-major order over the upper
+// triangle: g(i, j) = i N - i (i - 1) / 2 + (j - i).
+__host__ __device__ inline long long tri_start(long long i, long long N) {
+  return i * N - (i * (i - 1)) / 2;
+}
+// Inverse of g: the row i is the largest with tri_start(i) <= g (closed-form
+// estimate, then exact integer correction), j = g - tri_start(i) + i.
+__host__ __device__ inline void tri_decode(long long g, long long N, int* pi, int* pj) {
+  const double b = 2.0 * (double)N + 1.0;
+  double disc = b * b - 8.0 * (double)g;
+  if (disc < 0.0) disc = 0.0;
+  long long i = (long long)((b - sqrt(disc)) * 0.5);
+  if (i < 0) i = 0;
+  if (i > N - 1) i = N - 1;
+  while (i + 1 <= N - 1 && tri_start(i + 1, N) <= g) ++i;
+  while (i > 0 && tri_start(i, N) > g) --i;
+  *pi = (int)i;
+  *pj = (int)(g - tri_start(i, N) + i);
+}
+
+// ------------------------------------------------- size-independent kernels
+// Per-pair energy: E_ij = h^3 sum of the zconv block partials (one warp per
+// pair, fixed reduction order).
+__global__ void k_pair_energy(const double* __restrict__ epart, int nper,
+                              const int4* __restrict__ pairs, int npair, double h3,
+                              double* __restrict__ Epair) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= npair) return;
+  double s = 0.0;
+  for (int t = lane; t < nper; t += 32) s += epart[(long long)w * nper + t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) Epair[pairs[w].z] = h3 * s;
+}
+
+// E_x = -(alpha/2) sum_{i,j} f_i f_j E_ij = -(alpha/2) sum_{i<=j} (2 - d_ij) f_i f_j E_ij
+// (Eq. HF).  One block, fixed-order tree reduction; pairs decoded on device.
+__global__ void k_exx_total(const double* __restrict__ Epair, long long P, int N,
+                            const double* __restrict__ occ, double alpha, double* __restrict__ E) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long g = threadIdx.x; g < P; g += blockDim.x) {
+    int i, j;
+    tri_decode(g, N, &i, &j);
+    const double m = (i == j) ? 1.0 : 2.0;
+    s += m * occ[i] * occ[j] * Epair[g];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *E = -0.5 * alpha * red[0];
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+struct Tile {
+  int off, count;      // slice of the pair table
+  int i0, ti, j0, tj;  // orbital blocks
+  int diag;
+};
+
+}  // namespace exx
+
+using namespace exx;
+
+struct exx_plan_s {
+  int n = 0, N = 0, prec = 0, kind = 0;
+  unsigned flags = 0;
+  double h = 0.0, alpha = 0.0;
+  std::vector<double> occ;
+  const Ops* ops = nullptr;
+  int T = 0;
+  std::vector<Tile> tiles;
+  int maxpairs = 0;
+  long long P = 0;
+  size_t ws = 0;
+  int device = 0;
+  std::string err;
+  // device memory
+  void* Gs = nullptr;
+  void* tw = nullptr;
+  double* d_occ = nullptr;
+  int4* d_pairs = nullptr;
+  double* epart = nullptr;
+  double* Epair = nullptr;
+  void* X2 = nullptr;
+  void* V = nullptr;
+  double* vacc = nullptr;
+  double* E_dev = nullptr;
+};
+
+namespace {
+
+const char* kStatus[] = {"EXX_OK", "EXX_ERR_INVALID_ARG", "EXX_ERR_CUDA", "EXX_ERR_OOM",
+                         "EXX_ERR_TIMEOUT", "EXX_ERR_NOT_SUPPORTED"};
+
+exx_status_t cuda_fail(exx_plan_t p, cudaError_t e) {
+  if (p) p->err = cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? EXX_ERR_OOM : EXX_ERR_CUDA;
+}
+
+#define EXX_CUDA(p, call)                         \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_); \
+  } while (0)
+
+void free_plan(exx_plan_t p) {
+  void* ptrs[] = {p->Gs, p->tw, p->d_occ, p->d_pairs, p->epart, p->Epair, p->X2, p->V, p->vacc, p->E_dev};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+}
+
+template <typename T> exx_status_t dalloc(exx_plan_t p, T** out, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->err = cudaGetErrorString(e);
+    return EXX_ERR_OOM;
+  }
+  p->ws += bytes;
+  *out = static_cast<T*>(q);
+  return EXX_OK;
+}
+
+int default_tile(int N) {
+  const char* env = std::getenv("EXX_TILE");
+  int T = env ? std::atoi(env) : 8;
+  if (T < 1) T = 1;
+  if (T > 8) T = 8;
+  return T < N ? T : N;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* exx_status_string(exx_status_t s) {
+  return (s >= 0 && s <= EXX_ERR_NOT_SUPPORTED) ? kStatus[s] : "EXX_UNKNOWN_STATUS";
+}
+
+const char* exx_last_error(exx_plan_t p) { return p ? p->err.c_str() : ""; }
+
+const char* exx_version(void) { return "exx-gb300 0.1 (sm_103a)"; }
+
+exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double* out_host) {
+  if (n < 1 || !(h > 0.0) || out_host == nullptr) return EXX_ERR_INVALID_ARG;
+  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY) return EXX_ERR_INVALID_ARG;
+  return exx_host::kernel_spectrum_octant(n, h, kernel, out_host) ? EXX_OK : EXX_ERR_INVALID_ARG;
+}
+
+exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[3], double alpha,
+                             const double* occupations, int norb, int precision, int kernel,
+                             unsigned flags, void* cuda_stream) {
+  if (out == nullptr) return EXX_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (grid == nullptr || h == nullptr || occupations == nullptr) return EXX_ERR_INVALID_ARG;
+  if (norb < 1 || grid[0] < 2 || grid[1] < 2 || grid[2] < 2) return EXX_ERR_INVALID_ARG;
+  if (!(h[0] > 0.0) || !(h[1] > 0.0) || !(h[2] > 0.0) || !std::isfinite(alpha))
+    return EXX_ERR_INVALID_ARG;
+  if (precision != EXX_FP64 && precision != EXX_FP32) return EXX_ERR_INVALID_ARG;
+  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY) return EXX_ERR_INVALID_ARG;
+  if (flags & ~(unsigned)EXX_FLAG_VX_FP64) return EXX_ERR_INVALID_ARG;
+  for (int i = 0; i < norb; ++i)
+    if (!std::isfinite(occupations[i])) return EXX_ERR_INVALID_ARG;
+  if (grid[0] != grid[1] || grid[0] != grid[2] || h[0] != h[1] || h[0] != h[2])
+    return EXX_ERR_NOT_SUPPORTED;
+  const int n = grid[0];
+  if (split_l1(2 * n) == 0) return EXX_ERR_NOT_SUPPORTED;
+  const Ops* ops = lookup_ops(precision, n);
+  if (ops == nullptr || !ops->supported) return EXX_ERR_NOT_SUPPORTED;
+
+  exx_plan_t p = new exx_plan_s();
+  p->n = n;
+  p->N = norb;
+  p->prec = precision;
+  p->kind = kernel;
+  p->flags = flags;
+  p->h = h[0];
+  p->alpha = alpha;
+  p->occ.assign(occupations, occupations + norb);
+  p->ops = ops;
+  p->P = (long long)norb * (norb + 1) / 2;
+  cudaGetDevice(&p->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+  // pair tiles: blocks of T orbitals, tiles (bi, bj) with bi <= bj
+  p->T = default_tile(norb);
+  const int T = p->T;
+  const int nb = (norb + T - 1) / T;
+  std::vector<int4> pairs;
+  for (int bi = 0; bi < nb; ++bi)
+    for (int bj = bi; bj < nb; ++bj) {
+      Tile t;
+      t.i0 = bi * T;
+      t.ti = std::min(T, norb - t.i0);
+      t.j0 = bj * T;
+      t.tj = std::min(T, norb - t.j0);
+      t.diag = (bi == bj);
+      t.off = (int)pairs.size();
+      for (int a = 0; a < t.ti; ++a)
+        for (int b = t.diag ? a : 0; b < t.tj; ++b) {
+          const int i = t.i0 + a, j = t.j0 + b;
+          pairs.push_back(make_int4(i, j, (int)tri_start(i, norb) + (j - i), 0));
+        }
+      t.count = (int)pairs.size() - t.off;
+      p->maxpairs = std::max(p->maxpairs, t.count);
+      p->tiles.push_back(t);
+    }
+
+  // kernel spectrum (FP64, host), scaled by the inverse-FFT normalisation
+  const size_t m = (size_t)n + 1;
+  std::vector<double> Gh(m * m * m);
+  if (!exx_host::kernel_spectrum_octant(n, p->h, kernel, Gh.data())) {
+    delete p;
+    return EXX_ERR_INVALID_ARG;
+  }
+  const double L = 2.0 * n;
+  const double scale = 1.0 / (L * L * L);
+  const size_t rs = precision == EXX_FP64 ? sizeof(double) : sizeof(float);
+  const size_t cs = 2 * rs;
+  std::vector<unsigned char> gbuf(m * m * m * rs), twbuf(2 * n * cs);
+  for (size_t k = 0; k < m * m * m; ++k) {
+    const double g = Gh[k] * scale;
+    if (precision == EXX_FP64) reinterpret_cast<double*>(gbuf.data())[k] = g;
+    else reinterpret_cast<float*>(gbuf.data())[k] = (float)g;
+  }
+  for (int k = 0; k < 2 * n; ++k) {
+    const double a = -M_PI * (double)k / (double)n;  // -2 pi k / (2n)
+    const double c = std::cos(a), s = std::sin(a);
+    if (precision == EXX_FP64) {
+      reinterpret_cast<double*>(twbuf.data())[2 * k] = c;
+      reinterpret_cast<double*>(twbuf.data())[2 * k + 1] = s;
+    } else {
+      reinterpret_cast<float*>(twbuf.data())[2 * k] = (float)c;
+      reinterpret_cast<float*>(twbuf.data())[2 * k + 1] = (float)s;
+    }
+  }
+
+  const long long n3 = (long long)n * n * n;
+  const size_t nper = m * (size_t)ops->nyb;
+  exx_status_t st_;
+#define EXX_ALLOC(ptr, bytes)                 \
+  if ((st_ = dalloc(p, &(ptr), (bytes))) != EXX_OK) { \
+    free_plan(p);                             \
+    delete p;                                 \
+    return st_;                               \
+  }
+  EXX_ALLOC(p->Gs, gbuf.size());
+  EXX_ALLOC(p->tw, twbuf.size());
+  EXX_ALLOC(p->d_occ, norb * sizeof(double));
+  EXX_ALLOC(p->d_pairs, pairs.size() * sizeof(int4));
+  EXX_ALLOC(p->epart, (size_t)p->maxpairs * nper * sizeof(double));
+  EXX_ALLOC(p->Epair, (size_t)p->P * sizeof(double));
+  EXX_ALLOC(p->X2, (size_t)p->maxpairs * m * n * (2 * n) * cs);
+  EXX_ALLOC(p->V, (size_t)p->maxpairs * n3 * rs);
+  if (precision == EXX_FP32 && !(flags & EXX_FLAG_VX_FP64)) {
+    EXX_ALLOC(p->vacc, (size_t)norb * n3 * sizeof(double));
+  }
+  EXX_ALLOC(p->E_dev, sizeof(double));
+#undef EXX_ALLOC
+
+  cudaError_t e = cudaMemcpyAsync(p->Gs, gbuf.data(), gbuf.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->tw, twbuf.data(), twbuf.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_occ, p->occ.data(), norb * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_pairs, pairs.data(), pairs.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = ops->setup();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    delete p;
+    return e == cudaErrorMemoryAllocation ? EXX_ERR_OOM : EXX_ERR_CUDA;
+  }
+  *out = p;
+  return EXX_OK;
+}
+
+exx_status_t exx_plan_destroy(exx_plan_t p) {
+  if (p == nullptr) return EXX_OK;
+  free_plan(p);
+  delete p;
+  return EXX_OK;
+}
+
+exx_status_t exx_plan_info(exx_plan_t p, int* tile, int* ntiles, size_t* workspace_bytes,
+                           int* launches_apply, int* launches_energy) {
+  if (p == nullptr) return EXX_ERR_INVALID_ARG;
+  const int nt = (int)p->tiles.size();
+  if (tile) *tile = p->T;
+  if (ntiles) *ntiles = nt;
+  if (workspace_bytes) *workspace_bytes = p->ws;
+  const bool conv = p->vacc != nullptr;
+  if (launches_apply) *launches_apply = 5 * nt + 1 + (conv ? 1 : 0);
+  if (launches_energy) *launches_energy = 3 * nt + 1;
+  return EXX_OK;
+}
+
+static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_dev, bool apply,
+                        cudaStream_t st) {
+  const int n = p->n, N = p->N;
+  const long long n3 = (long long)n * n * n;
+  const double h3 = p->h * p->h * p->h;
+  const int nper = (n + 1) * p->ops->nyb;
+  const size_t rs = p->prec == EXX_FP64 ? sizeof(double) : sizeof(float);
+  double* acc = nullptr;
+  if (apply) {
+    acc = p->vacc ? p->vacc : static_cast<double*>(vxpsi);
+    EXX_CUDA(p, cudaMemsetAsync(acc, 0, (size_t)N * n3 * sizeof(double), st));
+  }
+  const double c = -p->alpha;
+  for (const Tile& t : p->tiles) {
+    const int4* pr = p->d_pairs + t.off;
+    p->ops->fwd_xy(psi, pr, t.count, p->X2, p->tw, n3, st);
+    p->ops->zconv(p->X2, p->Gs, p->tw, p->epart, t.count, !apply, st);
+    k_pair_energy<<<(t.count * 32 + 255) / 256, 256, 0, st>>>(p->epart, nper, pr, t.count, h3, p->Epair);
+    if (apply) {
+      p->ops->inv_yx(p->X2, p->V, p->tw, t.count, st);
+      const int threads = 256;
+      long long blocks = (n3 + threads - 1) / threads;
+      if (blocks > 152 * 16) blocks = 152 * 16;
+      if (p->prec == EXX_FP64)
+        k_accum<double, 8><<<(int)blocks, threads, 0, st>>>(
+            static_cast<const double*>(psi), static_cast<const double*>(p->V), acc, p->d_occ, t.i0,
+            t.ti, t.j0, t.tj, t.diag, c, n3);
+      else
+        k_accum<float, 8><<<(int)blocks, threads, 0, st>>>(
+            static_cast<const float*>(psi), static_cast<const float*>(p->V), acc, p->d_occ, t.i0,
+            t.ti, t.j0, t.tj, t.diag, c, n3);
+    }
+  }
+  k_exx_total<<<1, 256, 0, st>>>(p->Epair, p->P, N, p->d_occ, p->alpha, E_dev ? E_dev : p->E_dev);
+  if (apply && p->vacc) {
+    const long long tot = (long long)N * n3;
+    long long blocks = (tot + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_to_float<<<(int)blocks, 256, 0, st>>>(p->vacc, static_cast<float*>(vxpsi), tot);
+  }
+  (void)rs;
+  EXX_CUDA(p, cudaGetLastError());
+  return EXX_OK;
+}
+
+exx_status_t exx_apply_async(exx_plan_t p, const void* psi, void* vxpsi, double* E_dev,
+                             void* cuda_stream) {
+  if (p == nullptr || psi == nullptr || vxpsi == nullptr) return EXX_ERR_INVALID_ARG;
+  return run(p, psi, vxpsi, E_dev, true, static_cast<cudaStream_t>(cuda_stream));
+}
+
+exx_status_t exx_energy_async(exx_plan_t p, const void* psi, double* E_dev, void* cuda_stream) {
+  if (p == nullptr || psi == nullptr) return EXX_ERR_INVALID_ARG;
+  return run(p, psi, nullptr, E_dev, false, static_cast<cudaStream_t>(cuda_stream));
+}
+
+exx_status_t exx_apply(exx_plan_t p, const void* psi, void* vxpsi, double* E_out, void* cuda_stream) {
+  if (p == nullptr || psi == nullptr || vxpsi == nullptr) return EXX_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  exx_status_t s = run(p, psi, vxpsi, nullptr, true, st);
+  if (s != EXX_OK || E_out == nullptr) return s;
+  EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  EXX_CUDA(p, cudaStreamSynchronize(st));
+  return EXX_OK;
+}
+
+exx_status_t exx_energy(exx_plan_t p, const void* psi, double* E_out, void* cuda_stream) {
+  if (p == nullptr || psi == nullptr || E_out == nullptr) return EXX_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  exx_status_t s = run(p, psi, nullptr, nullptr, false, st);
+  if (s != EXX_OK) return s;
+  EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  EXX_CUDA(p, cudaStreamSynchronize(st));
+  return EXX_OK;
+}
+
+exx_status_t exx_pair_energies(exx_plan_t p, double* out_host, void* cuda_stream) {
+  if (p == nullptr || out_host == nullptr) return EXX_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  EXX_CUDA(p, cudaMemcpyAsync(out_host, p->Epair, (size_t)p->P * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+  EXX_CUDA(p, cudaStreamSynchronize(st));
+  return EXX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,311 @@
+// Register-resident mixed-radix DFTs for the exact-exchange Poisson path.
+//
+// Every transform length used on the path is 2n = L = L1 * L2 with small
+// factors of 2, 3, 5 and 7.  A line of length L is transformed by the
+// four-step (two-pass) decomposition: L2 sub-DFTs of length L1, a twiddle,
+// then L1 sub-DFTs of length L2.  Each sub-DFT runs entirely in one thread's
+// registers (fully unrolled, twiddles known at compile time); the exchange
+// between the two passes goes through shared memory.
+//
+// Zero padding (Sec. 2.1.2 of arXiv 1712.07973: the free-boundary convolution
+// is computed exactly with a padded FFT) makes half of every forward input
+// and half of every inverse output unneeded; dft_halfin / dft_halfout prune
+// the first / last butterfly level accordingly.
+//
+// Sign convention: SIGN = -1 forward (exp(-2 pi i nk/P)), +1 inverse, both
+// unnormalised.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <utility>
+
+#ifndef EXX_HD
+#define EXX_HD __host__ __device__ __forceinline__
+#endif
+
+namespace exx {
+
+// ---------------------------------------------------------------- complex
+template <typename R> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+template <typename R> using cplx = typename cvec<R>::type;
+
+template <typename C> struct creal;
+template <> struct creal<float2> { using type = float; };
+template <> struct creal<double2> { using type = double; };
+
+template <typename C>
+EXX_HD C mkc(typename creal<C>::type x, typename creal<C>::type y) {
+  C r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename C> EXX_HD C cadd(C a, C b) { return mkc<C>(a.x + b.x, a.y + b.y); }
+template <typename C> EXX_HD C csub(C a, C b) { return mkc<C>(a.x - b.x, a.y - b.y); }
+template <typename C> EXX_HD C cmul(C a, C b) {
+  return mkc<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> EXX_HD C cmulc(C a, C b) {
+  return mkc<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> EXX_HD C cscale(C a, typename creal<C>::type s) {
+  return mkc<C>(a.x * s, a.y * s);
+}
+template <typename C> EXX_HD C cconj(C a) { return mkc<C>(a.x, -a.y); }
+// multiply by i * SIGN  (SIGN = +1: i, SIGN = -1: -i)
+template <int SIGN, typename C> EXX_HD C mul_si(C a) {
+  return SIGN > 0 ? mkc<C>(-a.y, a.x) : mkc<C>(a.y, -a.x);
+}
+
+// ------------------------------------------------- compile-time trigonometry
+// cos / sin of 2 pi num / den: exact reduction of the rational argument to
+// the nearest quarter turn, |x| <= pi/4, then the Taylor series (Horner form,
+// 13 terms: the first neglected term is below 1e-22).
+__host__ __device__ constexpr double tsin_q(double x) {
+  const double x2 = x * x;
+  double s = 0.0;
+  for (int k = 13; k >= 1; --k) s = 1.0 - s * x2 / ((2.0 * k) * (2.0 * k + 1.0));
+  return x * s;
+}
+__host__ __device__ constexpr double tcos_q(double x) {
+  const double x2 = x * x;
+  double s = 0.0;
+  for (int k = 13; k >= 1; --k) s = 1.0 - s * x2 / ((2.0 * k - 1.0) * (2.0 * k));
+  return s;
+}
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+__host__ __device__ constexpr long pmod(long a, long m) { return ((a % m) + m) % m; }
+// 2 pi a / den = q * pi/2 + x with q = nearest quarter, x = 2 pi (4a - q den) / (4 den)
+__host__ __device__ constexpr long quarter(long a, long den) { return (8 * a + den) / (2 * den); }
+__host__ __device__ constexpr double cos2pi(long num, long den) {
+  const long a = pmod(num, den);
+  const long q = quarter(a, den);
+  const double x = (kTwoPi / (4.0 * den)) * (double)(4 * a - q * den);
+  const double c = tcos_q(x), s = tsin_q(x);
+  switch (q & 3) {
+    case 0: return c;
+    case 1: return -s;
+    case 2: return -c;
+    default: return s;
+  }
+}
+__host__ __device__ constexpr double sin2pi(long num, long den) {
+  const long a = pmod(num, den);
+  const long q = quarter(a, den);
+  const double x = (kTwoPi / (4.0 * den)) * (double)(4 * a - q * den);
+  const double c = tcos_q(x), s = tsin_q(x);
+  switch (q & 3) {
+    case 0: return s;
+    case 1: return c;
+    case 2: return -s;
+    default: return -c;
+  }
+}
+
+// compile-time loop: f is called with ic<0>, ic<1>, ... (usable as constants)
+template <int I> struct ic {
+  static constexpr int value = I;
+  __host__ __device__ constexpr operator int() const { return I; }
+};
+template <int... I, typename F>
+EXX_HD void sfor_impl(std::integer_sequence<int, I...>, F&& f) {
+  (f(ic<I>{}), ...);
+}
+template <int N, typename F> EXX_HD void sfor(F&& f) {
+  sfor_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// omega^e with omega = exp(SIGN 2 pi i / P), as a compile-time constant
+template <int SIGN, int P, int E, typename C> EXX_HD C twc() {
+  using R = typename creal<C>::type;
+  constexpr double c = cos2pi(E, P);
+  constexpr double s = SIGN * sin2pi(E, P);
+  return mkc<C>((R)c, (R)s);
+}
+template <int SIGN, int P, int E, typename C> EXX_HD C twmul(C a) {
+  constexpr long e = pmod(E, P);
+  if constexpr (e == 0) {
+    return a;
+  } else if constexpr (4 * e == P) {  // omega^{P/4} = SIGN i
+    return mul_si<SIGN>(a);
+  } else if constexpr (2 * e == P) {
+    return mkc<C>(-a.x, -a.y);
+  } else if constexpr (4 * e == 3 * P) {
+    return mul_si<-SIGN>(a);
+  } else if constexpr (8 * e == P || 8 * e == 3 * P || 8 * e == 5 * P || 8 * e == 7 * P) {
+    // odd multiples of pi/4: (+-1 +- i)/sqrt2 with a single scale
+    using R = typename creal<C>::type;
+    constexpr double r = 0.70710678118654752440084436210485;
+    constexpr double c = cos2pi(E, P) > 0 ? 1.0 : -1.0;
+    constexpr double s = (SIGN * sin2pi(E, P)) > 0 ? 1.0 : -1.0;
+    // (c + i s) * (a.x + i a.y) * r
+    return mkc<C>((R)r * ((R)c * a.x - (R)s * a.y), (R)r * ((R)c * a.y + (R)s * a.x));
+  } else {
+    return cmul(a, twc<SIGN, P, E, C>());
+  }
+}
+
+// ------------------------------------------------------------ DFT kernels
+// v[S*i], i < P : in-place DFT, natural order in and out.
+
+template <int P> struct first_factor {
+  static constexpr int value = (P % 4 == 0 && P > 4) ? 4
+                               : (P % 2 == 0) ? 2
+                               : (P % 3 == 0) ? 3
+                               : (P % 5 == 0) ? 5
+                               : (P % 7 == 0) ? 7
+                                              : P;
+};
+
+template <int P, int S, int SIGN, typename C> EXX_HD void dft(C* v);
+
+template <int S, int SIGN, typename C> EXX_HD void dft2(C* v) {
+  C a = v[0], b = v[S];
+  v[0] = cadd(a, b);
+  v[S] = csub(a, b);
+}
+
+template <int S, int SIGN, typename C> EXX_HD void dft3(C* v) {
+  using R = typename creal<C>::type;
+  constexpr R h = (R)0.5;
+  constexpr R s3 = (R)(SIGN * 0.86602540378443864676372317075294);
+  C a = v[0], b = v[S], c = v[2 * S];
+  C t1 = cadd(b, c);
+  C t2 = mkc<C>(a.x - h * t1.x, a.y - h * t1.y);
+  C d = csub(b, c);
+  C t3 = mkc<C>(-s3 * d.y, s3 * d.x);  // i * s3 * (b - c)
+  v[0] = cadd(a, t1);
+  v[S] = cadd(t2, t3);
+  v[2 * S] = csub(t2, t3);
+}
+
+template <int S, int SIGN, typename C> EXX_HD void dft4(C* v) {
+  C a = v[0], b = v[S], c = v[2 * S], d = v[3 * S];
+  C s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = mul_si<SIGN>(csub(b, d));
+  v[0] = cadd(s0, s2);
+  v[2 * S] = csub(s0, s2);
+  v[S] = cadd(s1, s3);
+  v[3 * S] = csub(s1, s3);
+}
+
+// odd prime P: X_k = x0 + sum_{j=1}^{(P-1)/2} [(x_j + x_{P-j}) cos(2 pi jk/P)
+//                                               + SIGN i (x_j - x_{P-j}) sin(2 pi jk/P)]
+template <int P, int S, int SIGN, typename C> EXX_HD void dft_prime(C* v) {
+  using R = typename creal<C>::type;
+  constexpr int H = (P - 1) / 2;
+  C sp[H], sm[H];
+  sfor<H>([&](auto J) {
+    constexpr int j = J + 1;
+    sp[J] = cadd(v[j * S], v[(P - j) * S]);
+    sm[J] = csub(v[j * S], v[(P - j) * S]);
+  });
+  C x0 = v[0];
+  C tot = x0;
+  sfor<H>([&](auto J) { tot = cadd(tot, sp[J]); });
+  sfor<H>([&](auto K) {
+    constexpr int k = K + 1;
+    R re = x0.x, im = x0.y, qre = 0, qim = 0;
+    sfor<H>([&](auto J) {
+      constexpr int j = J + 1;
+      constexpr R c = (R)cos2pi((long)j * k, P);
+      constexpr R s = (R)(SIGN * sin2pi((long)j * k, P));
+      re += c * sp[J].x;
+      im += c * sp[J].y;
+      qre -= s * sm[J].y;  // i*s*(sm) real part = -s*sm.y
+      qim += s * sm[J].x;
+    });
+    v[k * S] = mkc<C>(re + qre, im + qim);
+    v[(P - k) * S] = mkc<C>(re - qre, im - qim);
+  });
+  v[0] = tot;
+}
+
+// composite P = A * B (A = first factor): input n = B*n1 + n2, output k1 + A*k2
+template <int P, int S, int SIGN, typename C> EXX_HD void dft_composite(C* v) {
+  constexpr int A = first_factor<P>::value;
+  constexpr int B = P / A;
+  // step 1: B DFTs of length A over n1 (stride B*S), in place
+  sfor<B>([&](auto N2) { dft<A, B * S, SIGN>(v + N2 * S); });
+  // twiddle: element at (B*k1 + n2) *= omega_P^{n2 k1}
+  sfor<A>([&](auto K1) {
+    sfor<B>([&](auto N2) {
+      constexpr int idx = (B * K1 + N2) * S;
+      v[idx] = twmul<SIGN, P, (int)(N2 * K1)>(v[idx]);
+    });
+  });
+  // step 2: A DFTs of length B over n2 (contiguous blocks of B)
+  sfor<A>([&](auto K1) { dft<B, S, SIGN>(v + B * K1 * S); });
+  // position (B*k1 + k2) holds X[k1 + A*k2]: transpose to natural order
+  C t[P];
+  sfor<A>([&](auto K1) { sfor<B>([&](auto K2) { t[K1 + A * K2] = v[(B * K1 + K2) * S]; }); });
+  sfor<P>([&](auto I) { v[I * S] = t[I]; });
+}
+
+template <int P, int S, int SIGN, typename C> EXX_HD void dft(C* v) {
+  if constexpr (P == 1) {
+  } else if constexpr (P == 2) {
+    dft2<S, SIGN>(v);
+  } else if constexpr (P == 3) {
+    dft3<S, SIGN>(v);
+  } else if constexpr (P == 4) {
+    dft4<S, SIGN>(v);
+  } else if constexpr (P == 5 || P == 7) {
+    dft_prime<P, S, SIGN>(v);
+  } else {
+    static_assert(first_factor<P>::value != P, "DFT length with a prime factor > 7");
+    dft_composite<P, S, SIGN>(v);
+  }
+}
+
+// Pruned input: only v[0..P/2) are nonzero (the rest is ignored).  Output all
+// P values in natural order.  X[2k] = DFT_{P/2}(x), X[2k+1] = DFT_{P/2}(x w^j).
+template <int P, int SIGN, typename C> EXX_HD void dft_halfin(C* v) {
+  static_assert(P % 2 == 0, "pruned DFT needs an even length");
+  constexpr int H = P / 2;
+  C e[H], o[H];
+  sfor<H>([&](auto J) {
+    e[J] = v[J];
+    o[J] = twmul<SIGN, P, (int)J>(v[J]);
+  });
+  dft<H, 1, SIGN>(e);
+  dft<H, 1, SIGN>(o);
+  sfor<H>([&](auto K) {
+    v[2 * K] = e[K];
+    v[2 * K + 1] = o[K];
+  });
+}
+
+// Pruned output: all P inputs, only outputs y[0..P/2) are produced (into
+// v[0..P/2)).  y[j] = DFT_{P/2}(x_even)[j] + w^j DFT_{P/2}(x_odd)[j].
+template <int P, int SIGN, typename C> EXX_HD void dft_halfout(C* v) {
+  static_assert(P % 2 == 0, "pruned DFT needs an even length");
+  constexpr int H = P / 2;
+  C e[H], o[H];
+  sfor<H>([&](auto J) {
+    e[J] = v[2 * J];
+    o[J] = v[2 * J + 1];
+  });
+  dft<H, 1, SIGN>(e);
+  dft<H, 1, SIGN>(o);
+  sfor<H>([&](auto J) { v[J] = cadd(e[J], twmul<SIGN, P, (int)J>(o[J])); });
+}
+
+// Four-step split of a line length L = L1 * L2: L1 even (pruning), L1 <= 16,
+// L2 <= 20, both with factors in {2, 3, 5, 7}.
+__host__ __device__ constexpr bool smooth7(int p) {
+  while (p % 2 == 0) p /= 2;
+  while (p % 3 == 0) p /= 3;
+  while (p % 5 == 0) p /= 5;
+  while (p % 7 == 0) p /= 7;
+  return p == 1;
+}
+__host__ __device__ constexpr int split_l1(int L) {
+  for (int a = 16; a >= 2; a -= 2)
+    if (L % a == 0 && L / a <= 20 && smooth7(a) && smooth7(L / a)) return a;
+  return 0;
+}
+
+}  // namespace exx

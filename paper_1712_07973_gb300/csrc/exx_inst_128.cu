@@ -1,0 +1,3 @@
+// Kernel instantiations of the exact-exchange pipeline for n = 128.
+#include "exx_ops.cuh"
+EXX_DEFINE_OPS(128)

@@ -1,0 +1,10 @@
+// Kernel instantiations of the exact-exchange pipeline for n = 2 3 4 5 6 7 8 9.
+#include "exx_ops.cuh"
+EXX_DEFINE_OPS(2)
+EXX_DEFINE_OPS(3)
+EXX_DEFINE_OPS(4)
+EXX_DEFINE_OPS(5)
+EXX_DEFINE_OPS(6)
+EXX_DEFINE_OPS(7)
+EXX_DEFINE_OPS(8)
+EXX_DEFINE_OPS(9)

@@ -1,0 +1,5 @@
+// Kernel instantiations of the exact-exchange pipeline for n = 48 56 64.
+#include "exx_ops.cuh"
+EXX_DEFINE_OPS(48)
+EXX_DEFINE_OPS(56)
+EXX_DEFINE_OPS(64)

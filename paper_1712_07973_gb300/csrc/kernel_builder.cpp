@@ -1,0 +1,214 @@
+// Host-side FP64 builder of the free-boundary Poisson kernel spectrum.
+//
+// The paper solves lap V_ij = -4 pi rho_ij by convolving rho_ij with a Green's
+// function discretised on the uniform mesh, exactly, through an FFT on a grid
+// zero-padded to 2n points per axis (arXiv 1712.07973, Sec. 2.1.2).  It does
+// not print the discretisation; this library uses the band-limited kernel
+//
+//   G[m] = h^3 G_BL(m h),  G_BL(r) = (2 pi)^-3 int_{|k_d| <= pi/h} 4 pi/k^2 e^{ik.r} d^3k,
+//
+// (the exact potential of densities band-limited to the mesh's Brillouin zone)
+// or, on request, the point-sampled Hockney kernel h^3/|m h|.
+//
+// Route used here (distinct from the FP64 oracle's real-space route): with
+// 1/r = (2/sqrt pi) int_0^inf exp(-t^2 r^2) dt every term of the t-integral is
+// separable, so the padded spectrum itself separates per t:
+//
+//   Ghat[kx,ky,kz] = h^2 (2/sqrt pi) int_0^inf  gh(t,kx) gh(t,ky) gh(t,kz) dt,
+//   gh(t,k) = sum_{d=-(n-1)}^{n} g(t,d) cos(pi k d / n)          (windowed DFT)
+//   g(t,x)  = 1/(sqrt(pi) t) int_0^pi exp(-q^2/(4t^2)) cos(q x) dq (h = 1 units)
+//
+// The t-integral uses the exp-sinh rule t = exp(pi/2 sinh s) (double
+// exponential decay at both ends); g uses composite 16-point Gauss-Legendre in
+// q, or exp(-t^2 x^2) when t <= 0.2 (the neglected tail is below erfc(2.5 pi)).
+// The slot d = n of the periodic embedding is never reached by outputs in
+// [0, n) and carries G[n], which keeps the spectrum real and even.
+
+#include <cmath>
+#include <cstddef>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace exx_host {
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_m.
+void gauss_legendre(int m, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(m, 0.0);
+  w.assign(m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (m + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= m; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      // p1 = P_m(z), p0 = P_{m-1}(z)
+      dp = m * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Separable (t-node) spectrum: A[t][k] = sqrt-weighted gh(t,k); returns nt.
+void sinc_factors(int n, std::vector<double>& A, std::vector<double>& wt) {
+  // composite Gauss-Legendre on q in [0, pi]: one panel per cosine period of
+  // the largest distance, plus margin
+  const int gl = 16;
+  std::vector<double> gx, gw;
+  gauss_legendre(gl, gx, gw);
+  const int panels = n / 2 + 8;
+  const int nq = gl * panels;
+  std::vector<double> q(nq), qw(nq);
+  for (int p = 0; p < panels; ++p) {
+    double a = kPi * p / panels, b = kPi * (p + 1) / panels;
+    for (int i = 0; i < gl; ++i) {
+      q[p * gl + i] = 0.5 * (a + b) + 0.5 * (b - a) * gx[i];
+      qw[p * gl + i] = 0.5 * (b - a) * gw[i];
+    }
+  }
+  std::vector<double> cq((size_t)nq * (n + 1));
+  for (int j = 0; j < nq; ++j)
+    for (int d = 0; d <= n; ++d) cq[(size_t)j * (n + 1) + d] = std::cos(q[j] * d);
+  // windowed DFT matrix cos(pi k d / n) with end weights 1, 2, ..., 2, 1
+  std::vector<double> ck((size_t)(n + 1) * (n + 1));
+  for (int k = 0; k <= n; ++k)
+    for (int d = 0; d <= n; ++d) {
+      double c = (d == 0 || d == n) ? 1.0 : 2.0;
+      // exact argument reduction of k*d mod 2n keeps the cosine accurate
+      long r = ((long)k * d) % (2L * n);
+      ck[(size_t)k * (n + 1) + d] = c * std::cos(kPi * (double)r / n);
+    }
+  // exp-sinh nodes
+  const double step = 1.0 / 32.0;
+  const double smin = -4.5, smax = 3.6;
+  std::vector<double> ts, ws;
+  for (double s = smin; s <= smax + 1e-12; s += step) {
+    double t = std::exp(0.5 * kPi * std::sinh(s));
+    double dtds = 0.5 * kPi * std::cosh(s) * t;
+    ts.push_back(t);
+    ws.push_back(step * dtds);
+  }
+  const int nt = (int)ts.size();
+  A.assign((size_t)nt * (n + 1), 0.0);
+  wt = ws;
+  std::vector<double> g(n + 1);
+  for (int it = 0; it < nt; ++it) {
+    const double t = ts[it];
+    if (t <= 0.2) {
+      for (int d = 0; d <= n; ++d) g[d] = std::exp(-t * t * (double)d * d);
+    } else {
+      std::vector<double> e(nq);
+      for (int j = 0; j < nq; ++j) e[j] = qw[j] * std::exp(-q[j] * q[j] / (4.0 * t * t));
+      const double pre = 1.0 / (std::sqrt(kPi) * t);
+      for (int d = 0; d <= n; ++d) {
+        double acc = 0.0;
+        for (int j = 0; j < nq; ++j) acc += e[j] * cq[(size_t)j * (n + 1) + d];
+        g[d] = pre * acc;
+      }
+    }
+    for (int k = 0; k <= n; ++k) {
+      double acc = 0.0;
+      for (int d = 0; d <= n; ++d) acc += ck[(size_t)k * (n + 1) + d] * g[d];
+      A[(size_t)it * (n + 1) + k] = acc;
+    }
+  }
+}
+
+void sinc_spectrum(int n, double h, double* out) {
+  std::vector<double> A, wt;
+  sinc_factors(n, A, wt);
+  const int nt = (int)wt.size();
+  const int m = n + 1;
+  const double pre = h * h * 2.0 / std::sqrt(kPi);
+  // Ghat is symmetric under permutations of (kx, ky, kz) on a cubic grid:
+  // evaluate kz >= ky >= kx and mirror.
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int kz = 0; kz < m; ++kz) {
+    std::vector<double> b(nt);
+    for (int ky = 0; ky <= kz; ++ky) {
+      for (int it = 0; it < nt; ++it)
+        b[it] = wt[it] * A[(size_t)it * m + kz] * A[(size_t)it * m + ky];
+      for (int kx = 0; kx <= ky; ++kx) {
+        double acc = 0.0;
+        for (int it = 0; it < nt; ++it) acc += b[it] * A[(size_t)it * m + kx];
+        const double v = pre * acc;
+        const int p[3] = {kz, ky, kx};
+        // all 6 permutations
+        const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+        for (int q = 0; q < 6; ++q) {
+          const int a = p[perm[q][0]], bb = p[perm[q][1]], c = p[perm[q][2]];
+          out[((size_t)a * m + bb) * m + c] = v;
+        }
+      }
+    }
+  }
+}
+
+void hockney_spectrum(int n, double h, double* out) {
+  const int m = n + 1;
+  const double origin = 3.0 * std::log(2.0 + std::sqrt(3.0)) - 0.5 * kPi;
+  std::vector<double> G((size_t)m * m * m), T((size_t)m * m * m);
+  for (int z = 0; z < m; ++z)
+    for (int y = 0; y < m; ++y)
+      for (int x = 0; x < m; ++x) {
+        const double r = std::sqrt((double)x * x + (double)y * y + (double)z * z);
+        G[((size_t)z * m + y) * m + x] = h * h * (r > 0.0 ? 1.0 / r : origin);
+      }
+  std::vector<double> ck((size_t)m * m);
+  for (int k = 0; k < m; ++k)
+    for (int d = 0; d < m; ++d) {
+      double c = (d == 0 || d == n) ? 1.0 : 2.0;
+      long r = ((long)k * d) % (2L * n);
+      ck[(size_t)k * m + d] = c * std::cos(kPi * (double)r / n);
+    }
+  // three separable passes of the windowed cosine transform
+  for (int axis = 0; axis < 3; ++axis) {
+#pragma omp parallel for
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b)
+        for (int k = 0; k < m; ++k) {
+          double acc = 0.0;
+          for (int d = 0; d < m; ++d) {
+            size_t src;
+            if (axis == 0) src = ((size_t)a * m + b) * m + d;       // along x
+            else if (axis == 1) src = ((size_t)a * m + d) * m + b;  // along y
+            else src = ((size_t)d * m + a) * m + b;                 // along z
+            acc += ck[(size_t)k * m + d] * G[src];
+          }
+          size_t dst;
+          if (axis == 0) dst = ((size_t)a * m + b) * m + k;
+          else if (axis == 1) dst = ((size_t)a * m + k) * m + b;
+          else dst = ((size_t)k * m + a) * m + b;
+          T[dst] = acc;
+        }
+    G.swap(T);
+  }
+  for (size_t i = 0; i < G.size(); ++i) out[i] = G[i];
+}
+
+}  // namespace
+
+// kind: 0 = band-limited (sinc), 1 = Hockney.  out: (n+1)^3 doubles.
+bool kernel_spectrum_octant(int n, double h, int kind, double* out) {
+  if (n < 1 || !(h > 0.0) || out == nullptr) return false;
+  if (kind == 0) sinc_spectrum(n, h, out);
+  else if (kind == 1) hockney_spectrum(n, h, out);
+  else return false;
+  return true;
+}
+
+}  // namespace exx_host

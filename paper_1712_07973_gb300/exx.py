@@ -1,0 +1,201 @@
+"""Thin Python binding over the C ABI in ``include/exx.h`` (argument marshalling only).
+
+Every step of the exact-exchange pipeline runs in the CUDA library
+``_lib/libexx_gb300.so``; this module passes device pointers from PyTorch
+tensors and the current CUDA stream.  There is no CPU path: if the library or
+a CUDA device is missing, the calls raise.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["ExxError", "ExxPlan", "load_library", "kernel_spectrum", "EXPORTS",
+           "FP64", "FP32", "KERNEL_SINC", "KERNEL_HOCKNEY", "FLAG_VX_FP64"]
+
+FP64, FP32 = 0, 1
+KERNEL_SINC, KERNEL_HOCKNEY = 0, 1
+FLAG_VX_FP64 = 1
+STATUS = ["EXX_OK", "EXX_ERR_INVALID_ARG", "EXX_ERR_CUDA", "EXX_ERR_OOM", "EXX_ERR_TIMEOUT",
+          "EXX_ERR_NOT_SUPPORTED"]
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_size_p = ctypes.POINTER(ctypes.c_size_t)
+
+# name -> (restype, argtypes), one entry per declaration in include/exx.h
+EXPORTS = {
+    "exx_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _c_int_p, _c_double_p,
+                                       ctypes.c_double, _c_double_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_uint, ctypes.c_void_p]),
+    "exx_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_double_p, ctypes.c_void_p]),
+    "exx_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _c_double_p,
+                                 ctypes.c_void_p]),
+    "exx_apply_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "exx_energy_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "exx_pair_energies": (ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_void_p]),
+    "exx_plan_info": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, _c_size_p, _c_int_p,
+                                     _c_int_p]),
+    "exx_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "exx_kernel_spectrum": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _c_double_p]),
+    "exx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "exx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "exx_version": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+class ExxError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
+        self.status = status
+
+
+def load_library(path=None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        raise ExxError(1, "load_library",
+                       f"{path} is missing; build it with paper_1712_07973_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status, where, plan=None):
+    if status != 0:
+        detail = ""
+        if plan is not None:
+            detail = (load_library().exx_last_error(plan) or b"").decode()
+        raise ExxError(status, where, detail)
+
+
+def kernel_spectrum(n, h, kind=KERNEL_SINC):
+    """Host-only FP64 octant of the padded kernel spectrum, shape (n+1,)*3."""
+    out = np.zeros((n + 1) ** 3, dtype=np.float64)
+    _check(load_library().exx_kernel_spectrum(n, float(h), int(kind),
+                                              out.ctypes.data_as(_c_double_p)), "exx_kernel_spectrum")
+    return out.reshape(n + 1, n + 1, n + 1)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class ExxPlan:
+    """Plan of the exact-exchange operator for fixed grid, h, alpha and occupations.
+
+    precision: "fp64" (psi/vxpsi double) or "fp32" (psi float; vxpsi float, or
+    double with vx_fp64=True).  kernel: "sinc" (band-limited) or "hockney".
+    """
+
+    def __init__(self, n, h, alpha, occupations, precision="fp32", kernel="sinc",
+                 vx_fp64=False, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise ExxError(2, "ExxPlan", "no CUDA device: the EXX operator runs only on the GPU")
+        self.lib = load_library()
+        self.n = int(n)
+        self.h = float(h)
+        self.alpha = float(alpha)
+        occ = np.ascontiguousarray(np.asarray(occupations, dtype=np.float64))
+        self.occ = occ
+        self.norb = int(occ.size)
+        self.precision = {"fp64": FP64, "fp32": FP32}[precision]
+        self.kernel = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY}[kernel]
+        self.vx_fp64 = bool(vx_fp64)
+        self.dtype = torch.float64 if self.precision == FP64 else torch.float32
+        self.vx_dtype = torch.float64 if (self.precision == FP64 or self.vx_fp64) else torch.float32
+        grid = (ctypes.c_int * 3)(self.n, self.n, self.n)
+        hh = (ctypes.c_double * 3)(self.h, self.h, self.h)
+        handle = ctypes.c_void_p()
+        flags = FLAG_VX_FP64 if self.vx_fp64 else 0
+        _check(self.lib.exx_plan_create(ctypes.byref(handle), grid, hh, self.alpha,
+                                        occ.ctypes.data_as(_c_double_p), self.norb, self.precision,
+                                        self.kernel, flags, _stream_ptr(stream)), "exx_plan_create")
+        self.handle = handle
+
+    # ---------------------------------------------------------------- checks
+    def _psi(self, psi):
+        import torch
+        if not isinstance(psi, torch.Tensor) or not psi.is_cuda:
+            raise ExxError(1, "psi", "a CUDA tensor is required")
+        if psi.dtype != self.dtype:
+            raise ExxError(1, "psi", f"dtype {psi.dtype}, plan expects {self.dtype}")
+        if tuple(psi.shape) != (self.norb, self.n, self.n, self.n) or not psi.is_contiguous():
+            raise ExxError(1, "psi", f"contiguous shape {(self.norb,) + (self.n,) * 3} required")
+        return ctypes.c_void_p(psi.data_ptr())
+
+    def energy(self, psi, stream=None):
+        E = ctypes.c_double()
+        _check(self.lib.exx_energy(self.handle, self._psi(psi), ctypes.byref(E), _stream_ptr(stream)),
+               "exx_energy", self.handle)
+        return E.value
+
+    def apply(self, psi, out=None, stream=None):
+        import torch
+        p = self._psi(psi)
+        if out is None:
+            out = torch.empty(psi.shape, dtype=self.vx_dtype, device=psi.device)
+        elif out.dtype != self.vx_dtype or out.shape != psi.shape or not out.is_contiguous():
+            raise ExxError(1, "vxpsi", f"contiguous {self.vx_dtype} tensor of psi's shape required")
+        E = ctypes.c_double()
+        _check(self.lib.exx_apply(self.handle, p, ctypes.c_void_p(out.data_ptr()), ctypes.byref(E),
+                                  _stream_ptr(stream)), "exx_apply", self.handle)
+        return E.value, out
+
+    def apply_async(self, psi, out, E_dev=None, stream=None):
+        p = self._psi(psi)
+        e = ctypes.c_void_p(E_dev.data_ptr()) if E_dev is not None else ctypes.c_void_p()
+        _check(self.lib.exx_apply_async(self.handle, p, ctypes.c_void_p(out.data_ptr()), e,
+                                        _stream_ptr(stream)), "exx_apply_async", self.handle)
+
+    def energy_async(self, psi, E_dev=None, stream=None):
+        p = self._psi(psi)
+        e = ctypes.c_void_p(E_dev.data_ptr()) if E_dev is not None else ctypes.c_void_p()
+        _check(self.lib.exx_energy_async(self.handle, p, e, _stream_ptr(stream)),
+               "exx_energy_async", self.handle)
+
+    def pair_energies(self, stream=None):
+        P = self.norb * (self.norb + 1) // 2
+        out = np.zeros(P, dtype=np.float64)
+        _check(self.lib.exx_pair_energies(self.handle, out.ctypes.data_as(_c_double_p),
+                                          _stream_ptr(stream)), "exx_pair_energies", self.handle)
+        return out
+
+    def info(self):
+        t, nt, la, le = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ws = ctypes.c_size_t()
+        _check(self.lib.exx_plan_info(self.handle, ctypes.byref(t), ctypes.byref(nt),
+                                      ctypes.byref(ws), ctypes.byref(la), ctypes.byref(le)),
+               "exx_plan_info")
+        return {"tile": t.value, "ntiles": nt.value, "workspace_bytes": ws.value,
+                "launches_apply": la.value, "launches_energy": le.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.exx_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA pipeline (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP64 path 1e-10 relative (E_x, every E_ij, and Vx psi relative to
+its largest entry); FP32 path 1e-6 Ha absolute on E_x plus a relative bound on
+Vx psi that follows from single-precision FFT rounding (about 1e-6 of the
+largest entry: ~log2(2n) butterfly levels of 6e-8 each, three axes, forward
+and inverse).
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import exx_oracle as o
+from paper_1712_07973_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    from paper_1712_07973_gb300 import build
+    build.build()
+    return torch, torch.device("cuda:0")
+
+
+def _orbitals(n, N, seed, h=0.45, p_type=True):
+    r = synth.OrbitalRecipe(n=n, h=h, norb=N, nsites=max(2, N), seed=seed, gauss_per_orb=3,
+                            sigma=(0.12 * n * h, 0.2 * n * h), p_type=p_type)
+    return synth.make_orbitals(r)
+
+
+def _gpu(torch_dev, psi, occ, alpha, h, precision, kernel="sinc", vx_fp64=False):
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    n = psi.shape[1]
+    plan = exx.ExxPlan(n, h, alpha, occ, precision=precision, kernel=kernel, vx_fp64=vx_fp64)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    p = torch.from_numpy(psi).to(dev, dt)
+    E, vx = plan.apply(p)
+    Ee = plan.energy(p)
+    Eij = plan.pair_energies()
+    plan.close()
+    return E, Ee, vx.double().cpu().numpy(), Eij
+
+
+def _oracle(psi, occ, alpha, h, kernel=o.KERNEL_SINC):
+    n = psi.shape[1]
+    Gh = o.kernel_spectrum(o.kernel_real_space(n, h, kernel))
+    Ex, vx, Eij = o.exx(psi, occ, alpha, h, Gh)
+    return Ex, vx, Eij[np.triu_indices(psi.shape[0])]
+
+
+def _assert_fp64(got, ref):
+    E, Ee, vx, Eij = got
+    Eo, vxo, Eijo = ref
+    assert abs(E - Eo) <= 1e-10 * abs(Eo), (E, Eo)
+    assert abs(Ee - Eo) <= 1e-10 * abs(Eo), (Ee, Eo)
+    assert np.max(np.abs(Eij - Eijo)) <= 1e-10 * np.max(np.abs(Eijo))
+    assert np.max(np.abs(vx - vxo)) <= 1e-10 * np.max(np.abs(vxo))
+
+
+# sizes spanning every radix mix of 2n (2, 3, 5, 7) and both one-pass (2n <= 16)
+# and two-pass transforms, odd n included
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 18, 20, 24, 28, 36, 40])
+def test_fp64_all_radices(torch_dev, n):
+    N = 3 if n > 3 else 2
+    psi = _orbitals(n, N, seed=100 + n)
+    occ = np.array([2.0, 1.5, 0.5][:N])
+    h = 0.45
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, h, "fp64"), _oracle(psi, occ, 0.25, h))
+
+
+@pytest.mark.parametrize("n", [48, 56, 64])
+def test_fp64_larger_grids(torch_dev, n):
+    psi = _orbitals(n, 2, seed=7 + n, h=0.4)
+    occ = np.array([2.0, 2.0])
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.4, "fp64"), _oracle(psi, occ, 0.25, 0.4))
+
+
+def test_plain_fp64_workload_4_orbitals_n32(torch_dev):
+    # 4 orbitals on 32^3 (64^3 padded), h = 0.4, closed shell f = 2, alpha = 0.25
+    r, psi = synth.workload("c1_fp64_n32_N4")
+    occ = np.full(r.norb, r.occupation)
+    ref = _oracle(psi, occ, r.alpha, r.h)
+    got = _gpu(torch_dev, psi, occ, r.alpha, r.h, "fp64")
+    _assert_fp64(got, ref)
+    path = os.path.join(GOLDEN, "c1_fp64_n32_N4.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            g = json.load(fh)
+        assert abs(got[0] - g["E_x"]) <= 1e-10 * abs(g["E_x"])
+
+
+def test_hockney_kernel(torch_dev):
+    psi = _orbitals(10, 3, seed=5)
+    occ = np.array([2.0, 2.0, 2.0])
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.45, "fp64", kernel="hockney"),
+                 _oracle(psi, occ, 0.25, 0.45, o.KERNEL_HOCKNEY))
+
+
+def test_ragged_tiles_and_tile_size_invariance(torch_dev, monkeypatch):
+    # 11 orbitals: tiles of 8 leave a ragged 3-orbital block; a tile edge of 3
+    # gives a different schedule with the same results
+    psi = _orbitals(8, 11, seed=9)
+    occ = np.linspace(0.3, 2.0, 11)
+    ref = _oracle(psi, occ, 0.3, 0.45)
+    got8 = _gpu(torch_dev, psi, occ, 0.3, 0.45, "fp64")
+    _assert_fp64(got8, ref)
+    monkeypatch.setenv("EXX_TILE", "3")
+    got3 = _gpu(torch_dev, psi, occ, 0.3, 0.45, "fp64")
+    _assert_fp64(got3, ref)
+    monkeypatch.setenv("EXX_TILE", "1")
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.3, 0.45, "fp64"), ref)
+
+
+def test_degenerate_inputs(torch_dev):
+    # one orbital; zero occupations; identically zero orbitals
+    psi = _orbitals(8, 1, seed=3)
+    _assert_fp64(_gpu(torch_dev, psi, np.array([2.0]), 0.25, 0.45, "fp64"),
+                 _oracle(psi, np.array([2.0]), 0.25, 0.45))
+    psi = _orbitals(8, 3, seed=4)
+    occ = np.array([0.0, 2.0, 0.0])
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.45, "fp64"), _oracle(psi, occ, 0.25, 0.45))
+    E, Ee, vx, Eij = _gpu(torch_dev, np.zeros((2, 6, 6, 6)), np.array([2.0, 2.0]), 0.25, 0.45, "fp64")
+    assert E == 0.0 and Ee == 0.0 and not np.any(vx) and not np.any(Eij)
+
+
+def test_gaussian_exchange_closed_form_on_gpu(torch_dev):
+    # E_x of one normalised Gaussian orbital is -(alpha/2) f^2 / (sigma_rho sqrt(pi))
+    n, h, s = 48, 0.2, 0.6 * math.sqrt(2.0)
+    x = np.arange(n) * h - 0.5 * (n - 1) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    psi = ((math.pi * s * s) ** -0.75 * np.exp(-(X * X + Y * Y + Z * Z) / (2 * s * s)))[None]
+    E, _, _, _ = _gpu(torch_dev, psi, np.array([2.0]), 0.25, h, "fp64")
+    assert E == pytest.approx(-0.5 * 0.25 * 4.0 / (s / math.sqrt(2) * math.sqrt(math.pi)), rel=1e-10)
+
+
+def test_determinism(torch_dev):
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    psi = _orbitals(16, 5, seed=21)
+    for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        plan = exx.ExxPlan(16, 0.45, 0.25, np.full(5, 2.0), precision=prec)
+        p = torch.from_numpy(psi).to(dev, dt)
+        E1, v1 = plan.apply(p)
+        E2, v2 = plan.apply(p)
+        assert E1 == E2 and torch.equal(v1, v2)
+        plan.close()
+
+
+@pytest.mark.parametrize("n", [8, 12, 16, 24, 32, 48])
+def test_fp32_against_fp64_oracle(torch_dev, n):
+    N = 4
+    psi = _orbitals(n, N, seed=200 + n, h=0.4)
+    occ = np.full(N, 2.0)
+    Eo, vxo, Eijo = _oracle(psi, occ, 0.25, 0.4)
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, 0.25, 0.4, "fp32")
+    assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6, (E, Ee, Eo)
+    assert np.max(np.abs(Eij - Eijo)) <= 1e-6
+    assert np.max(np.abs(vx - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+    # the FP64-output flag returns the same accumulation without the final rounding
+    _, _, vx64, _ = _gpu(torch_dev, psi, occ, 0.25, 0.4, "fp32", vx_fp64=True)
+    assert np.max(np.abs(vx64 - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+    assert np.max(np.abs(vx64.astype(np.float32) - vx)) == 0.0
+
+
+def test_binding_rejects_wrong_tensors(torch_dev):
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    plan = exx.ExxPlan(8, 0.4, 0.25, [2.0, 2.0], precision="fp32")
+    with pytest.raises(exx.ExxError):
+        plan.energy(torch.zeros((2, 8, 8, 8), dtype=torch.float64, device=dev))
+    with pytest.raises(exx.ExxError):
+        plan.energy(torch.zeros((3, 8, 8, 8), dtype=torch.float32, device=dev))
+    with pytest.raises(exx.ExxError):
+        plan.energy(torch.zeros((2, 8, 8, 8), dtype=torch.float32))
+    plan.close()
+
+
+def test_fp32_workload_64_orbitals_n96_full_size(torch_dev):
+    # 64 orbitals on 96^3 (192^3 padded): the benchmark workload, same launch
+    # configuration as bench.py.  Expected values come from the stored oracle run.
+    path = os.path.join(GOLDEN, "c2_fp32_n96_N64.json")
+    if not os.path.exists(path):
+        pytest.skip("golden values not generated")
+    with open(path) as fh:
+        g = json.load(fh)
+    r, psi = synth.workload("c2_fp32_n96_N64")
+    fp = g["psi_fingerprint"]["abs_sum"]
+    got_fp = np.abs(psi.reshape(r.norb, -1)).sum(axis=1)
+    assert np.allclose(got_fp, fp, rtol=1e-10, atol=0), "input generator drifted"
+    occ = np.full(r.norb, r.occupation)
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, r.alpha, r.h, "fp32")
+    assert abs(E - g["E_x"]) <= 1e-6, (E, g["E_x"])
+    assert abs(Ee - g["E_x"]) <= 1e-6
+    assert np.max(np.abs(Eij - np.array(g["E_ij"]))) <= 1e-6
+    pts = np.array(g["sample_points"])
+    samples = vx[pts[:, 0], pts[:, 1], pts[:, 2], pts[:, 3]]
+    ref = np.array(g["vx_samples"])
+    scale = np.sqrt(max(g["vx_norm2"]) / (r.h ** 3 * r.n ** 3))
+    assert np.max(np.abs(samples - ref)) <= 2e-6 * max(np.max(np.abs(ref)), scale)
+    norms = np.array([r.h ** 3 * np.sum(v.astype(np.float64) ** 2) for v in vx])
+    assert np.allclose(norms, g["vx_norm2"], rtol=1e-5)
