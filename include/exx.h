@@ -137,6 +137,32 @@ exx_status_t exx_pair_energies(exx_plan_t plan, double* out_host, void* cuda_str
 exx_status_t exx_plan_info(exx_plan_t plan, int* tile, int* ntiles, size_t* workspace_bytes,
                            int* launches_apply, int* launches_energy);
 
+/*
+ * exx_apply_host -- exx_apply for callers whose orbitals live in host memory.
+ *   psi_host    host, [norb][n][n][n] (double for EXX_FP64, float for EXX_FP32);
+ *               page-locked memory gives asynchronous copies.
+ *   vxpsi_host  host, same shape, dtype as for exx_apply; overwritten.
+ *   E_out       host, may be NULL.
+ * The first call allocates device buffers for psi and vxpsi inside the plan
+ * (kept until exx_plan_destroy).  The call copies psi in, runs exx_apply on
+ * the stream, copies vxpsi and E_x out, and synchronises the stream.
+ */
+exx_status_t exx_apply_host(exx_plan_t plan, const void* psi_host, void* vxpsi_host, double* E_out,
+                            void* cuda_stream);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the launching stream around
+ * every launch of the pipeline (kernel kinds, in order: 0 fwd_xy, 1 zconv,
+ * 2 pair_energy, 3 inv_yx, 4 accum, 5 exx_total, 6 to_float).
+ * exx_profile_enable(plan, 1) starts recording (0 stops); exx_profile_read
+ * synchronises on the recorded events and returns, per kind, the summed
+ * milliseconds (host ms[EXX_NKINDS]) and launch counts (host
+ * launches[EXX_NKINDS]); reset != 0 clears the tallies afterwards.
+ */
+#define EXX_NKINDS 7
+exx_status_t exx_profile_enable(exx_plan_t plan, int enable);
+exx_status_t exx_profile_read(exx_plan_t plan, double* ms, long long* launches, int reset);
+
 /* exx_plan_destroy -- free the plan and its device memory (NULL is a no-op). */
 exx_status_t exx_plan_destroy(exx_plan_t plan);
 

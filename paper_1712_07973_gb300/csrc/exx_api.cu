@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -143,6 +144,14 @@ struct exx_plan_s {
   void* V = nullptr;
   double* vacc = nullptr;
   double* E_dev = nullptr;
+  void* h_psi = nullptr;  // exx_apply_host staging (allocated on first use)
+  void* h_vx = nullptr;
+  // per-kernel event timing (exx_profile_enable)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev[EXX_NKINDS];  // start/stop pairs, in launch order
+  size_t used[EXX_NKINDS] = {};
+  double ms[EXX_NKINDS] = {};
+  long long cnt[EXX_NKINDS] = {};
 };
 
 namespace {
@@ -162,10 +171,39 @@ exx_status_t cuda_fail(exx_plan_t p, cudaError_t e) {
   } while (0)
 
 void free_plan(exx_plan_t p) {
-  void* ptrs[] = {p->Gs, p->tw, p->d_occ, p->d_pairs, p->epart, p->Epair, p->X2, p->V, p->vacc, p->E_dev};
+  void* ptrs[] = {p->Gs,    p->tw, p->d_occ, p->d_pairs, p->epart, p->Epair, p->X2,
+                  p->V,     p->vacc, p->E_dev, p->h_psi, p->h_vx};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (int k = 0; k < EXX_NKINDS; ++k)
+    for (cudaEvent_t e : p->ev[k]) cudaEventDestroy(e);
 }
+
+enum Kind { K_FWD = 0, K_ZCONV = 1, K_PAIRE = 2, K_INV = 3, K_ACCUM = 4, K_TOTAL = 5, K_CONV = 6 };
+
+// Records a start/stop event pair on the launching stream around one launch.
+struct ProfScope {
+  exx_plan_t p;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t stop = nullptr;
+  ProfScope(exx_plan_t p_, int k, cudaStream_t s) : p(p_), kind(k), st(s) {
+    if (!p->prof) return;
+    std::vector<cudaEvent_t>& v = p->ev[kind];
+    size_t& u = p->used[kind];
+    while (v.size() < 2 * (u + 1)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      v.push_back(e);
+    }
+    cudaEventRecord(v[2 * u], st);
+    stop = v[2 * u + 1];
+    ++u;
+  }
+  ~ProfScope() {
+    if (stop) cudaEventRecord(stop, st);
+  }
+};
 
 template <typename T> exx_status_t dalloc(exx_plan_t p, T** out, size_t bytes) {
   void* q = nullptr;
@@ -276,7 +314,9 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
   const double scale = 1.0 / (L * L * L);
   const size_t rs = precision == EXX_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * rs;
-  std::vector<unsigned char> gbuf(m * m * m * rs), twbuf(2 * n * cs);
+  // twiddles exp(-2 pi i k / 2n): 2n high parts, then 2n low parts (the
+  // rounding residue of the high parts; zero in FP64)
+  std::vector<unsigned char> gbuf(m * m * m * rs), twbuf(2 * 2 * n * cs);
   for (size_t k = 0; k < m * m * m; ++k) {
     const double g = Gh[k] * scale;
     if (precision == EXX_FP64) reinterpret_cast<double*>(gbuf.data())[k] = g;
@@ -286,11 +326,17 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
     const double a = -M_PI * (double)k / (double)n;  // -2 pi k / (2n)
     const double c = std::cos(a), s = std::sin(a);
     if (precision == EXX_FP64) {
-      reinterpret_cast<double*>(twbuf.data())[2 * k] = c;
-      reinterpret_cast<double*>(twbuf.data())[2 * k + 1] = s;
+      double* t = reinterpret_cast<double*>(twbuf.data());
+      t[2 * k] = c;
+      t[2 * k + 1] = s;
+      t[4 * n + 2 * k] = 0.0;
+      t[4 * n + 2 * k + 1] = 0.0;
     } else {
-      reinterpret_cast<float*>(twbuf.data())[2 * k] = (float)c;
-      reinterpret_cast<float*>(twbuf.data())[2 * k + 1] = (float)s;
+      float* t = reinterpret_cast<float*>(twbuf.data());
+      t[2 * k] = (float)c;
+      t[2 * k + 1] = (float)s;
+      t[4 * n + 2 * k] = (float)(c - (double)(float)c);
+      t[4 * n + 2 * k + 1] = (float)(s - (double)(float)s);
     }
   }
 
@@ -371,26 +417,62 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
   const double c = -p->alpha;
   for (const Tile& t : p->tiles) {
     const int4* pr = p->d_pairs + t.off;
-    p->ops->fwd_xy(psi, pr, t.count, p->X2, p->tw, n3, st);
-    p->ops->zconv(p->X2, p->Gs, p->tw, p->epart, t.count, !apply, st);
-    k_pair_energy<<<(t.count * 32 + 255) / 256, 256, 0, st>>>(p->epart, nper, pr, t.count, h3, p->Epair);
+    {
+      ProfScope ps(p, K_FWD, st);
+      p->ops->fwd_xy(psi, pr, t.count, p->X2, p->tw, n3, st);
+    }
+    {
+      ProfScope ps(p, K_ZCONV, st);
+      p->ops->zconv(p->X2, p->Gs, p->tw, p->epart, t.count, !apply, st);
+    }
+    {
+      ProfScope ps(p, K_PAIRE, st);
+      k_pair_energy<<<(t.count * 32 + 255) / 256, 256, 0, st>>>(p->epart, nper, pr, t.count, h3,
+                                                                  p->Epair);
+    }
     if (apply) {
-      p->ops->inv_yx(p->X2, p->V, p->tw, t.count, st);
+      {
+        ProfScope ps(p, K_INV, st);
+        p->ops->inv_yx(p->X2, p->V, p->tw, t.count, st);
+      }
+      ProfScope ps(p, K_ACCUM, st);
       const int threads = 256;
-      long long blocks = (n3 + threads - 1) / threads;
-      if (blocks > 152 * 16) blocks = 152 * 16;
-      if (p->prec == EXX_FP64)
-        k_accum<double, 8><<<(int)blocks, threads, 0, st>>>(
-            static_cast<const double*>(psi), static_cast<const double*>(p->V), acc, p->d_occ, t.i0,
-            t.ti, t.j0, t.tj, t.diag, c, n3);
-      else
-        k_accum<float, 8><<<(int)blocks, threads, 0, st>>>(
-            static_cast<const float*>(psi), static_cast<const float*>(p->V), acc, p->d_occ, t.i0,
-            t.ti, t.j0, t.tj, t.diag, c, n3);
+      // vector width: 4 floats / 2 doubles per thread when n^3 and the
+      // caller's pointers allow aligned vector accesses
+      const bool al = ((uintptr_t)psi % 16 == 0) && ((uintptr_t)acc % 16 == 0);
+      const bool v4 = al && (n3 % 4) == 0;
+      const bool v2 = al && (n3 % 2) == 0;
+      if (p->prec == EXX_FP64) {
+        const int vec = v2 ? 2 : 1;
+        const long long blocks = (n3 / vec + threads - 1) / threads;
+        if (v2)
+          k_accum<double, 8, 2><<<(unsigned)blocks, threads, 0, st>>>(
+              static_cast<const double*>(psi), static_cast<const double*>(p->V), acc, p->d_occ,
+              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
+        else
+          k_accum<double, 8, 1><<<(unsigned)blocks, threads, 0, st>>>(
+              static_cast<const double*>(psi), static_cast<const double*>(p->V), acc, p->d_occ,
+              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
+      } else {
+        const int vec = v4 ? 4 : 1;
+        const long long blocks = (n3 / vec + threads - 1) / threads;
+        if (v4)
+          k_accum<float, 8, 4><<<(unsigned)blocks, threads, 0, st>>>(
+              static_cast<const float*>(psi), static_cast<const float*>(p->V), acc, p->d_occ,
+              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
+        else
+          k_accum<float, 8, 1><<<(unsigned)blocks, threads, 0, st>>>(
+              static_cast<const float*>(psi), static_cast<const float*>(p->V), acc, p->d_occ,
+              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
+      }
     }
   }
-  k_exx_total<<<1, 256, 0, st>>>(p->Epair, p->P, N, p->d_occ, p->alpha, E_dev ? E_dev : p->E_dev);
+  {
+    ProfScope ps(p, K_TOTAL, st);
+    k_exx_total<<<1, 256, 0, st>>>(p->Epair, p->P, N, p->d_occ, p->alpha, E_dev ? E_dev : p->E_dev);
+  }
   if (apply && p->vacc) {
+    ProfScope ps(p, K_CONV, st);
     const long long tot = (long long)N * n3;
     long long blocks = (tot + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
@@ -429,6 +511,57 @@ exx_status_t exx_energy(exx_plan_t p, const void* psi, double* E_out, void* cuda
   if (s != EXX_OK) return s;
   EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
   EXX_CUDA(p, cudaStreamSynchronize(st));
+  return EXX_OK;
+}
+
+exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host, double* E_out,
+                            void* cuda_stream) {
+  if (p == nullptr || psi_host == nullptr || vxpsi_host == nullptr) return EXX_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t cnt = (size_t)p->N * p->n * p->n * p->n;
+  const size_t ps = p->prec == EXX_FP64 ? sizeof(double) : sizeof(float);
+  const size_t vs = (p->prec == EXX_FP64 || (p->flags & EXX_FLAG_VX_FP64)) ? sizeof(double) : sizeof(float);
+  if (p->h_psi == nullptr) {
+    exx_status_t s = dalloc(p, &p->h_psi, cnt * ps);
+    if (s != EXX_OK) return s;
+  }
+  if (p->h_vx == nullptr) {
+    exx_status_t s = dalloc(p, &p->h_vx, cnt * vs);
+    if (s != EXX_OK) return s;
+  }
+  EXX_CUDA(p, cudaMemcpyAsync(p->h_psi, psi_host, cnt * ps, cudaMemcpyHostToDevice, st));
+  exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st);
+  if (s != EXX_OK) return s;
+  EXX_CUDA(p, cudaMemcpyAsync(vxpsi_host, p->h_vx, cnt * vs, cudaMemcpyDeviceToHost, st));
+  if (E_out) EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  EXX_CUDA(p, cudaStreamSynchronize(st));
+  return EXX_OK;
+}
+
+exx_status_t exx_profile_enable(exx_plan_t p, int enable) {
+  if (p == nullptr) return EXX_ERR_INVALID_ARG;
+  p->prof = enable != 0;
+  return EXX_OK;
+}
+
+exx_status_t exx_profile_read(exx_plan_t p, double* ms, long long* launches, int reset) {
+  if (p == nullptr) return EXX_ERR_INVALID_ARG;
+  for (int k = 0; k < EXX_NKINDS; ++k) {
+    for (size_t u = 0; u < p->used[k]; ++u) {
+      float t = 0.0f;
+      EXX_CUDA(p, cudaEventSynchronize(p->ev[k][2 * u + 1]));
+      EXX_CUDA(p, cudaEventElapsedTime(&t, p->ev[k][2 * u], p->ev[k][2 * u + 1]));
+      p->ms[k] += t;
+      p->cnt[k] += 1;
+    }
+    p->used[k] = 0;
+    if (ms) ms[k] = p->ms[k];
+    if (launches) launches[k] = p->cnt[k];
+    if (reset) {
+      p->ms[k] = 0.0;
+      p->cnt[k] = 0;
+    }
+  }
   return EXX_OK;
 }
 

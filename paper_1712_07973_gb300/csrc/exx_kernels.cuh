@@ -5,14 +5,13 @@
 //
 //   fwd_xy  (one CTA per z-slab and pair)
 //           rho = psi_i psi_j on the slab, real-to-complex FFT of length 2n
-//           along x with x >= n zero (two real lines packed per complex
-//           line), then the pruned complex FFT of length 2n along y with
-//           y >= n zero.  Writes X2[pair][kx][z][ky], kx in [0, n].
+//           along x with x >= n zero, then the pruned complex FFT of length
+//           2n along y (y >= n zero).  Writes X[pair][kx][z][ky].
 //   zconv   (one CTA per 32 columns (kx, ky) and pair)
 //           along z: pruned forward FFT (z >= n zero), multiply by the real
 //           kernel spectrum Ghat (Sec. 2.1.2; scaled by 1/(2n)^3), Parseval
 //           energy sum w(kx) Ghat |rho_hat|^2, inverse FFT keeping z < n.
-//           In place on X2 (becomes X3).
+//           In place on X.
 //   inv_yx  (one CTA per z-slab and pair)
 //           inverse FFT along y keeping y < n, complex-to-real FFT along x
 //           keeping x < n: V_ij on the n^3 mesh.
@@ -21,12 +20,22 @@
 //           (Vx psi)_j += -alpha f_i V_ij psi_i (Eq. daction); FP32 sums
 //           over the tile, FP64 accumulation across tiles, deterministic.
 //
-// Layouts: psi[o][z][y][x]; X2/X3[p][kx][z][ky] complex; V[p][z][y][x].
+// Layouts: psi[o][z][y][x]; X[p][kx][z][ky] complex; V[p][z][y][x].
 #pragma once
 
 #include "exx_fft.cuh"
 
 namespace exx {
+
+// Split of the x axis: a real line of length 2n is transformed as a complex
+// line of length n (even samples + i odd samples), n = LX1 * LX2.  LX1 is even
+// when n is even, so that the half of the input beyond the data is pruned.
+__host__ __device__ constexpr int split_x(int n) {
+  for (int a = 2; a <= 16; a += 2)
+    if (n % a == 0 && n / a <= 20 && smooth7(a) && smooth7(n / a)) return a;
+  if (n % 2 == 1 && n <= 16 && smooth7(n)) return n;
+  return 0;
+}
 
 // Padded scratch layout of one line in the [a][k1] form of the four-step:
 // slot(a, k1) = a * (L1 + 1) + k1; the line stride is odd so that lines of
@@ -39,19 +48,25 @@ template <int L1, int L2> struct Scr {
 template <typename R> __device__ __forceinline__ R sq(R a) { return a * a; }
 
 // ------------------------------------------------------------------ fwd_xy
-template <typename R, int N, int NT, int Q>
-__global__ void __launch_bounds__(NT)
-k_fwd_xy(const R* __restrict__ psi, const int4* __restrict__ pairs, cplx<R>* __restrict__ X2,
+// One CTA per (z-slab, pair).  Shared memory holds the slab Sl[k][y] (row
+// stride SP = n + 1).  x: the complex length-n FFT of z[m] = rho[2m] + i
+// rho[2m+1] runs in place in column y of Sl, followed by the split into the
+// Hermitian half spectrum X[k], k = 0..n (row n is the Nyquist row).  y: the
+// pruned length-2n FFT per kx row, written to HBM as X[p][kx][z][ky].
+template <typename R, int N, int NT, int MINB, int Q>
+__global__ void __launch_bounds__(NT, MINB)
+k_fwd_xy(const R* __restrict__ psi, const int4* __restrict__ pairs, cplx<R>* __restrict__ X,
          const cplx<R>* __restrict__ tw_g, long long n3) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
-  constexpr int NH = (N + 1) / 2;  // packed line pairs
-  using S_ = Scr<L1, L2>;
+  constexpr int X1 = split_x(N), X2 = N / X1;
+  constexpr bool PX = (N % 2) == 0;  // pruned x input
+  constexpr int XIN = PX ? X1 / 2 : X1;
+  constexpr int SP = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* Sl = tw + L;                       // [(N+1)][N]
-  C* S = Sl + (N + 1) * N;              // [Q][line]
-  R* stg = reinterpret_cast<R*>(S + Q * S_::line);  // [2Q][N]
+  C* tw = reinterpret_cast<C*>(smem_raw);  // [2L]: high parts, then low parts
+  C* twl = tw + L;
+  C* Sl = tw + 2 * L;  // [(N+1)][SP]
 
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
@@ -59,84 +74,94 @@ k_fwd_xy(const R* __restrict__ psi, const int4* __restrict__ pairs, cplx<R>* __r
   const int4 pr = pairs[p];
   const R* __restrict__ pi = psi + (long long)pr.x * n3 + (long long)z * N * N;
   const R* __restrict__ pj = psi + (long long)pr.y * n3 + (long long)z * N * N;
-  for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
+  for (int t = tid; t < 2 * L; t += NT) tw[t] = tw_g[t];
+  __syncthreads();
 
-  // ---- x: real-to-complex, two lines (y, y+1) packed as re + i im
-  for (int q0 = 0; q0 < NH; q0 += Q) {
-    const int nq = min(Q, NH - q0);
-    for (int idx = tid; idx < 2 * Q * N; idx += NT) {
-      const int r = idx / N, x = idx - r * N;
-      const int y = 2 * q0 + r;
-      stg[idx] = (r < 2 * nq && y < N) ? pi[y * N + x] * pj[y * N + x] : R(0);
-    }
-    __syncthreads();
-    for (int u = tid; u < nq * L2; u += NT) {
-      const int qq = u / L2, n2 = u - qq * L2;
-      C v[L1];
+  // x, pass 1: units (y, n2), n2 fastest (coalesced reads of row y)
+  for (int u = tid; u < N * X2; u += NT) {
+    const int y = u / X2, n2 = u - y * X2;
+    const R* ri = pi + y * N;
+    const R* rj = pj + y * N;
+    C v[X1];
 #pragma unroll
-      for (int n1 = 0; n1 < H1; ++n1) {
-        const int x = L2 * n1 + n2;
-        v[n1] = mkc<C>(stg[(2 * qq) * N + x], stg[(2 * qq + 1) * N + x]);
-      }
-      dft_halfin<L1, -1>(v);
-      C* s = S + qq * S_::line + n2 * S_::row;
-      s[0] = v[0];
-#pragma unroll
-      for (int k1 = 1; k1 < L1; ++k1) s[k1] = cmul(v[k1], tw[n2 * k1]);
+    for (int n1 = 0; n1 < XIN; ++n1) {
+      const int m = X2 * n1 + n2;
+      const R a = (2 * m < N) ? ri[2 * m] * rj[2 * m] : R(0);
+      const R b = (2 * m + 1 < N) ? ri[2 * m + 1] * rj[2 * m + 1] : R(0);
+      v[n1] = mkc<C>(a, b);
     }
-    __syncthreads();
-    for (int u = tid; u < nq * L1; u += NT) {
-      const int qq = u / L1, k1 = u - qq * L1;
-      C v[L2];
-      C* s = S + qq * S_::line + k1;
+    if constexpr (PX) {
+      dft_halfin<X1, -1, true>(v);
+    } else {
 #pragma unroll
-      for (int n2 = 0; n2 < L2; ++n2) v[n2] = s[n2 * S_::row];
-      dft<L2, 1, -1>(v);
+      for (int n1 = XIN; n1 < X1; ++n1) v[n1] = mkc<C>(R(0), R(0));
+      dft<X1, 1, -1, true>(v);
+    }
+    C* col = Sl + (n2 * X1) * SP + y;
+    col[0] = v[0];
 #pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) s[k2 * S_::row] = v[k2];
-    }
-    __syncthreads();
-    // unpack the two real lines: A = (C[k] + conj C[L-k]) / 2,
-    //                            B = (C[k] - conj C[L-k]) / (2i)
-    for (int u = tid; u < (N + 1) * nq; u += NT) {
-      const int k = u / nq, qq = u - k * nq;
-      const int km = (L - k) % L;
-      const C* s = S + qq * S_::line;
-      const C c = s[(k / L1) * S_::row + (k % L1)];
-      const C d = s[(km / L1) * S_::row + (km % L1)];
-      const C A = mkc<C>(R(0.5) * (c.x + d.x), R(0.5) * (c.y - d.y));
-      const C B = mkc<C>(R(0.5) * (c.y + d.y), R(-0.5) * (c.x - d.x));
-      const int y = 2 * (q0 + qq);
-      Sl[k * N + y] = A;
-      if (y + 1 < N) Sl[k * N + y + 1] = B;
-    }
-    __syncthreads();
+    for (int k1 = 1; k1 < X1; ++k1)  // omega_n^{n2 k1} = omega_2n^{2 n2 k1}
+      col[k1 * SP] = cmul2<true>(v[k1], tw[2 * n2 * k1], twl[2 * n2 * k1]);
   }
-
-  // ---- y: pruned forward FFT per kx row, straight to global memory
+  __syncthreads();
+  // x, pass 2: units (y, k1), y fastest; in place, natural order Z[k] at row k
+  for (int u = tid; u < N * X1; u += NT) {
+    const int k1 = u / N, y = u - k1 * N;
+    C v[X2];
+#pragma unroll
+    for (int n2 = 0; n2 < X2; ++n2) v[n2] = Sl[(n2 * X1 + k1) * SP + y];
+    dft<X2, 1, -1, true>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < X2; ++k2) Sl[(k1 + X1 * k2) * SP + y] = v[k2];
+  }
+  __syncthreads();
+  // split: X[k] = E[k] + w^k O[k], X[n-k] = conj(E[k] - w^k O[k]), with
+  // E = (Z[k] + conj Z[n-k]) / 2, O = (Z[k] - conj Z[n-k]) / (2i), w = omega_2n
+  for (int u = tid; u < N * (N / 2 + 1); u += NT) {
+    const int k = u / N, y = u - k * N;
+    if (k == 0) {
+      const C z0 = Sl[y];
+      Sl[y] = mkc<C>(z0.x + z0.y, R(0));
+      Sl[N * SP + y] = mkc<C>(z0.x - z0.y, R(0));
+    } else if (2 * k == N) {
+      const C zk = Sl[k * SP + y];
+      Sl[k * SP + y] = mkc<C>(zk.x, -zk.y);
+    } else {
+      const C zk = Sl[k * SP + y], zm = Sl[(N - k) * SP + y];
+      const C e = mkc<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+      const C o = mkc<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+      const C t = cmul2<true>(o, tw[k], twl[k]);
+      Sl[k * SP + y] = cadd(e, t);
+      Sl[(N - k) * SP + y] = mkc<C>(e.x - t.x, t.y - e.y);
+    }
+  }
+  __syncthreads();
+  // y: pruned length-2n FFT per kx row in batches of Q rows; pass 1 into the
+  // row scratch S (padded [n2][k1] layout), pass 2 straight to HBM
+  C* S = Sl + (N + 1) * SP;
   for (int r0 = 0; r0 <= N; r0 += Q) {
     const int nr = min(Q, N + 1 - r0);
     for (int u = tid; u < nr * L2; u += NT) {
       const int r = u / L2, n2 = u - r * L2;
-      const C* row = Sl + (r0 + r) * N;
+      const C* row = Sl + (r0 + r) * SP;
       C v[L1];
 #pragma unroll
       for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
-      dft_halfin<L1, -1>(v);
-      C* s = S + r * S_::line + n2 * S_::row;
-      s[0] = v[0];
+      dft_halfin<L1, -1, true>(v);
+      C* o = S + r * Scr<L1, L2>::line + n2 * Scr<L1, L2>::row;
+      o[0] = v[0];
 #pragma unroll
-      for (int k1 = 1; k1 < L1; ++k1) s[k1] = cmul(v[k1], tw[n2 * k1]);
+      for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul2<true>(v[k1], tw[n2 * k1], twl[n2 * k1]);
     }
     __syncthreads();
     for (int u = tid; u < nr * L1; u += NT) {
       const int r = u / L1, k1 = u - r * L1;
+      const C* q = S + r * Scr<L1, L2>::line + k1;
       C v[L2];
-      const C* s = S + r * S_::line + k1;
 #pragma unroll
-      for (int n2 = 0; n2 < L2; ++n2) v[n2] = s[n2 * S_::row];
-      dft<L2, 1, -1>(v);
-      C* out = X2 + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
+      for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
+      dft<L2, 1, -1, true>(v);
+      C* out = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
 #pragma unroll
       for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
     }
@@ -145,6 +170,11 @@ k_fwd_xy(const R* __restrict__ psi, const int4* __restrict__ pairs, cplx<R>* __r
 }
 
 // ------------------------------------------------------------------- zconv
+// One CTA per (32 consecutive ky columns, kx, pair); lane = column, warps
+// share the sub-DFTs of each pass.  Along z: pruned forward FFT (pass 1 of
+// length L1 over z = L2 n1 + n2, pass 2 of length L2), multiply by
+// Ghat/(2n)^3 with the Parseval energy w(kx) Ghat |rho_hat|^2, inverse FFT
+// keeping z < n.  In place on X.
 template <typename R, int N, int NW, bool ENERGY_ONLY>
 __global__ void __launch_bounds__(32 * NW)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
@@ -154,50 +184,53 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   constexpr int W = L < 32 ? L : 32;
   constexpr int M = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* buf = tw + L;  // [L slots][W]
+  C* tw = reinterpret_cast<C*>(smem_raw);  // [2L]: high parts, then low parts
+  C* twl = tw + L;
+  C* buf = tw + 2 * L;  // [L slots][W]
   __shared__ double red[NW];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int yb = blockIdx.x, kx = blockIdx.y, p = blockIdx.z;
   const int ky = yb * W + lane;
   const bool valid = lane < W && ky < L;
-  for (int t = tid; t < L; t += 32 * NW) tw[t] = tw_g[t];
+  for (int t = tid; t < 2 * L; t += 32 * NW) tw[t] = tw_g[t];
   C* col = X + (((long long)p * M + kx) * N) * L + (valid ? ky : 0);
   __syncthreads();
 
-  // forward, pass 1: L2 pruned DFTs of length L1 over z = L2 n1 + n2
+  // forward, pass 1
   for (int n2 = warp; n2 < L2; n2 += NW) {
     C v[L1];
 #pragma unroll
     for (int n1 = 0; n1 < H1; ++n1)
       v[n1] = valid ? col[(long long)(L2 * n1 + n2) * L] : mkc<C>(R(0), R(0));
-    dft_halfin<L1, -1>(v);
+    dft_halfin<L1, -1, true>(v);
     if (lane < W) {
       buf[(n2 * L1) * W + lane] = v[0];
 #pragma unroll
-      for (int k1 = 1; k1 < L1; ++k1) buf[(n2 * L1 + k1) * W + lane] = cmul(v[k1], tw[n2 * k1]);
+      for (int k1 = 1; k1 < L1; ++k1)
+        buf[(n2 * L1 + k1) * W + lane] = cmul2<true>(v[k1], tw[n2 * k1], twl[n2 * k1]);
     }
   }
   __syncthreads();
 
-  // pass 2 of the forward, kernel multiply, pass 1 of the inverse
+  // forward pass 2, kernel multiply, energy, inverse pass 1
   const int kyf = ky <= N ? ky : L - ky;
   const R* __restrict__ Gk = Gs + (long long)kx * M * M + (valid ? kyf : 0);
   double eacc = 0.0;
   for (int k1 = warp; k1 < L1; k1 += NW) {
     C v[L2];
 #pragma unroll
-    for (int n2 = 0; n2 < L2; ++n2) v[n2] = lane < W ? buf[(n2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
-    dft<L2, 1, -1>(v);
+    for (int n2 = 0; n2 < L2; ++n2)
+      v[n2] = lane < W ? buf[(n2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
+    dft<L2, 1, -1, true>(v);
     R es = R(0);
 #pragma unroll
     for (int k2 = 0; k2 < L2; ++k2) {
       const int kz = k1 + L1 * k2;
       const int kzf = kz <= N ? kz : L - kz;
-      const R g = valid ? __ldg(Gk + kzf * M) : R(0);
-      es += g * (sq(v[k2].x) + sq(v[k2].y));
-      v[k2] = cscale(v[k2], g);
+      const R gv = valid ? __ldg(Gk + kzf * M) : R(0);
+      es += gv * (sq(v[k2].x) + sq(v[k2].y));
+      v[k2] = cscale(v[k2], gv);
     }
     eacc += (double)es;
     if constexpr (!ENERGY_ONLY) {
@@ -211,11 +244,12 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   }
   if constexpr (!ENERGY_ONLY) {
     __syncthreads();
-    // inverse, pass 2: L2 DFTs of length L1, only z = L2 m1 + m2 < n kept
+    // inverse, pass 2: only z = L2 m1 + m2 < n is kept
     for (int m2 = warp; m2 < L2; m2 += NW) {
       C v[L1];
 #pragma unroll
-      for (int k1 = 0; k1 < L1; ++k1) v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
+      for (int k1 = 0; k1 < L1; ++k1)
+        v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
       dft_halfout<L1, 1>(v);
       if (valid) {
 #pragma unroll
@@ -238,156 +272,212 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 }
 
 // ------------------------------------------------------------------ inv_yx
-template <typename R, int N, int NT, int Q>
-__global__ void __launch_bounds__(NT)
-k_inv_yx(const cplx<R>* __restrict__ X3, R* __restrict__ V, const cplx<R>* __restrict__ tw_g) {
+// One CTA per (z-slab, pair).  y: inverse FFT of each kx row (pruned output
+// y < n) from HBM into the slab Sl[kx][y]; x: the Hermitian half
+// spectrum of each line is folded into a complex length-n spectrum
+// Z[k] = E'[k] + i O'[k] (E' = X[k] + conj X[n-k], O' = (X[k] - conj X[n-k])
+// w^-k), whose inverse FFT (in place in column y) gives the even and odd
+// samples of the real line: V[2m] = Re, V[2m+1] = Im, kept for x < n.
+template <typename R, int N, int NT, int MINB, int Q>
+__global__ void __launch_bounds__(NT, MINB)
+k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __restrict__ tw_g) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
-  constexpr int NH = (N + 1) / 2;
-  using S_ = Scr<L1, L2>;
+  constexpr int X1 = split_x(N), X2 = N / X1;
+  constexpr bool PX = (N % 2) == 0;
+  constexpr int XOUT = PX ? X1 / 2 : X1;
+  constexpr int SP = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);
-  C* Sl = tw + L;           // [(N+1)][N]
-  C* S = Sl + (N + 1) * N;  // [Q][line]
+  C* tw = reinterpret_cast<C*>(smem_raw);  // high parts
+  C* Sl = tw + L;                          // [(N+1)][SP]
 
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
   const int p = blockIdx.y;
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
   __syncthreads();
-
-  // ---- y: inverse FFT per kx row, keep y < n
+  // y: inverse length-2n FFT per kx row in batches of Q rows, keeping y < n;
+  // pass 1 (DFT_L2 over k2, twiddle) from HBM into the row scratch S, pass 2
+  // (pruned-output DFT_L1 over k1) into the slab
+  C* S = Sl + (N + 1) * SP;
   for (int r0 = 0; r0 <= N; r0 += Q) {
     const int nr = min(Q, N + 1 - r0);
     for (int u = tid; u < nr * L1; u += NT) {
       const int r = u / L1, k1 = u - r * L1;
-      const C* in = X3 + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
+      const C* in = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
       C v[L2];
 #pragma unroll
       for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
       dft<L2, 1, 1>(v);
-      C* s = S + r * S_::line + k1;
-      s[0] = v[0];
+      C* q = S + r * Scr<L1, L2>::line + k1;
+      q[0] = v[0];
 #pragma unroll
-      for (int m2 = 1; m2 < L2; ++m2) s[m2 * S_::row] = cmulc(v[m2], tw[m2 * k1]);
+      for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], tw[m2 * k1]);
     }
     __syncthreads();
     for (int u = tid; u < nr * L2; u += NT) {
       const int r = u / L2, m2 = u - r * L2;
-      const C* s = S + r * S_::line + m2 * S_::row;
+      const C* q = S + r * Scr<L1, L2>::line + m2 * Scr<L1, L2>::row;
       C v[L1];
 #pragma unroll
-      for (int k1 = 0; k1 < L1; ++k1) v[k1] = s[k1];
+      for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
       dft_halfout<L1, 1>(v);
-      C* row = Sl + (r0 + r) * N;
+      C* row = Sl + (r0 + r) * SP;
 #pragma unroll
       for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
     }
     __syncthreads();
   }
-
-  // ---- x: complex-to-real, two lines packed: C[k] = A[k] + i B[k] with the
-  //      Hermitian extension A[L-k] = conj A[k]; real parts of A, B are the lines
-  for (int q0 = 0; q0 < NH; q0 += Q) {
-    const int nq = min(Q, NH - q0);
-    for (int u = tid; u < nq * L1; u += NT) {
-      const int k1 = u / nq, qq = u - k1 * nq;
-      const int y = 2 * (q0 + qq);
-      C v[L2];
-#pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) {
-        const int k = k1 + L1 * k2;
-        const int kk = k <= N ? k : L - k;
-        C a = Sl[kk * N + y];
-        C b = (y + 1 < N) ? Sl[kk * N + y + 1] : mkc<C>(R(0), R(0));
-        if (kk == 0 || kk == N) {
-          a.y = R(0);
-          b.y = R(0);
-        }
-        if (k > N) {
-          a.y = -a.y;
-          b.y = -b.y;
-        }
-        v[k2] = mkc<C>(a.x - b.y, a.y + b.x);
-      }
-      dft<L2, 1, 1>(v);
-      C* s = S + qq * S_::line + k1;
-      s[0] = v[0];
-#pragma unroll
-      for (int m2 = 1; m2 < L2; ++m2) s[m2 * S_::row] = cmulc(v[m2], tw[m2 * k1]);
+  // fold the half spectrum into Z (units (y, k), k = 0..n/2, y fastest)
+  for (int u = tid; u < N * (N / 2 + 1); u += NT) {
+    const int k = u / N, y = u - k * N;
+    if (k == 0) {
+      const R x0 = Sl[y].x, xn = Sl[N * SP + y].x;
+      Sl[y] = mkc<C>(x0 + xn, x0 - xn);
+    } else if (2 * k == N) {
+      const C xk = Sl[k * SP + y];
+      Sl[k * SP + y] = mkc<C>(R(2) * xk.x, R(-2) * xk.y);
+    } else {
+      const C xk = Sl[k * SP + y], xm = Sl[(N - k) * SP + y];
+      const C e = mkc<C>(xk.x + xm.x, xk.y - xm.y);
+      const C d = mkc<C>(xk.x - xm.x, xk.y + xm.y);
+      const C o = cmulc(d, tw[k]);
+      Sl[k * SP + y] = mkc<C>(e.x - o.y, e.y + o.x);
+      Sl[(N - k) * SP + y] = mkc<C>(e.x + o.y, o.x - e.y);
     }
-    __syncthreads();
-    for (int u = tid; u < nq * L2; u += NT) {
-      const int qq = u / L2, m2 = u - qq * L2;
-      const C* s = S + qq * S_::line + m2 * S_::row;
-      C v[L1];
+  }
+  __syncthreads();
+  // x inverse, pass 1: units (y, k1), y fastest; in place over rows k1 + X1 k2
+  for (int u = tid; u < N * X1; u += NT) {
+    const int k1 = u / N, y = u - k1 * N;
+    C v[X2];
 #pragma unroll
-      for (int k1 = 0; k1 < L1; ++k1) v[k1] = s[k1];
-      dft_halfout<L1, 1>(v);
-      const int y = 2 * (q0 + qq);
-      R* out = V + ((long long)p * N + z) * N * N + (long long)y * N;
+    for (int k2 = 0; k2 < X2; ++k2) v[k2] = Sl[(k1 + X1 * k2) * SP + y];
+    dft<X2, 1, 1>(v);
+    Sl[k1 * SP + y] = v[0];
 #pragma unroll
-      for (int m1 = 0; m1 < H1; ++m1) {
-        const int x = L2 * m1 + m2;
-        out[x] = v[m1].x;
-        if (y + 1 < N) out[N + x] = v[m1].y;
-      }
+    for (int m2 = 1; m2 < X2; ++m2) Sl[(m2 * X1 + k1) * SP + y] = cmulc(v[m2], tw[2 * m2 * k1]);
+  }
+  __syncthreads();
+  // x inverse, pass 2: units (y, m2), m2 fastest (coalesced writes of row y)
+  R* Vz = V + ((long long)p * N + z) * N * N;
+  for (int u = tid; u < N * X2; u += NT) {
+    const int y = u / X2, m2 = u - y * X2;
+    C v[X1];
+#pragma unroll
+    for (int k1 = 0; k1 < X1; ++k1) v[k1] = Sl[(m2 * X1 + k1) * SP + y];
+    if constexpr (PX) dft_halfout<X1, 1>(v);
+    else dft<X1, 1, 1>(v);
+    R* row = Vz + (long long)y * N;
+#pragma unroll
+    for (int m1 = 0; m1 < XOUT; ++m1) {
+      const int m = X2 * m1 + m2;
+      if (2 * m < N) row[2 * m] = v[m1].x;
+      if (2 * m + 1 < N) row[2 * m + 1] = v[m1].y;
     }
-    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------- accum
 // One pair tile: orbitals i0..i0+ti-1 (block I) and j0..j0+tj-1 (block J);
 // off-diagonal tiles hold all ti*tj pairs (slot a*tj + b), diagonal tiles
-// (I == J) the ti(ti+1)/2 pairs a <= b in row-major order.
-template <typename R, int TM>
+// (I == J) the ti(ti+1)/2 pairs a <= b in row-major order.  Each thread owns
+// VEC consecutive mesh points (vector loads); the J loop is outermost so that
+// only the I-side partial sums stay live.
+template <typename R, int VEC> struct vecty;
+template <> struct vecty<float, 4> { using type = float4; };
+template <> struct vecty<float, 1> { using type = float; };
+template <> struct vecty<double, 2> { using type = double2; };
+template <> struct vecty<double, 1> { using type = double; };
+
+template <typename R, int VEC>
+__device__ __forceinline__ void vload(const R* p, R (&v)[VEC]) {
+  if constexpr (VEC == 1) {
+    v[0] = *p;
+  } else {
+    using V = typename vecty<R, VEC>::type;
+    const V t = *reinterpret_cast<const V*>(p);
+    const R* q = reinterpret_cast<const R*>(&t);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) v[e] = q[e];
+  }
+}
+// vx[0..VEC) += c * a  (FP64)
+template <typename R, int VEC>
+__device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
+  if constexpr (VEC == 4) {
+    double2* q = reinterpret_cast<double2*>(p);
+    double2 u = q[0], w = q[1];
+    u.x += c * (double)a[0];
+    u.y += c * (double)a[1];
+    w.x += c * (double)a[2];
+    w.y += c * (double)a[3];
+    q[0] = u;
+    q[1] = w;
+  } else if constexpr (VEC == 2) {
+    double2* q = reinterpret_cast<double2*>(p);
+    double2 u = q[0];
+    u.x += c * (double)a[0];
+    u.y += c * (double)a[1];
+    q[0] = u;
+  } else {
+    p[0] += c * (double)a[0];
+  }
+}
+
+template <typename R, int TM, int VEC>
 __global__ void __launch_bounds__(256)
 k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__ vx,
         const double* __restrict__ occ, int i0, int ti, int j0, int tj, int diag, double c,
         long long n3) {
-  R fi[TM], fj[TM];
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
+  if (r >= n3) return;
+  R fi[TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a) fi[a] = a < ti ? (R)occ[i0 + a] : R(0);
+  R pi[TM][VEC], ai[TM][VEC];
 #pragma unroll
   for (int a = 0; a < TM; ++a) {
-    fi[a] = a < ti ? (R)occ[i0 + a] : R(0);
-    fj[a] = a < tj ? (R)occ[j0 + a] : R(0);
-  }
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n3;
-       r += (long long)gridDim.x * blockDim.x) {
-    R pi[TM], pj[TM], ai[TM], aj[TM];
+    if (a < ti) vload<R, VEC>(psi + (long long)(i0 + a) * n3 + r, pi[a]);
 #pragma unroll
-    for (int a = 0; a < TM; ++a) {
-      pi[a] = a < ti ? psi[(long long)(i0 + a) * n3 + r] : R(0);
-      pj[a] = (!diag && a < tj) ? psi[(long long)(j0 + a) * n3 + r] : pi[a];
-      ai[a] = R(0);
-      aj[a] = R(0);
+    for (int e = 0; e < VEC; ++e) ai[a][e] = R(0);
+  }
+#pragma unroll
+  for (int b = 0; b < TM; ++b) {
+    if (b >= tj) break;
+    const R fb = (R)occ[j0 + b];
+    R pb[VEC], aj[VEC];
+    if (diag) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) pb[e] = pi[b][e];
+    } else {
+      vload<R, VEC>(psi + (long long)(j0 + b) * n3 + r, pb);
     }
 #pragma unroll
-    for (int a = 0; a < TM; ++a) {
-      if (a >= ti) continue;
+    for (int e = 0; e < VEC; ++e) aj[e] = R(0);
 #pragma unroll
-      for (int b = 0; b < TM; ++b) {
-        if (b >= tj) continue;
-        if (diag && b < a) continue;
-        const int slot = diag ? a * tj - (a * (a - 1)) / 2 + (b - a) : a * tj + b;
-        const R v = V[(long long)slot * n3 + r];
-        ai[a] += fj[b] * v * pj[b];
-        if (!(diag && a == b)) aj[b] += fi[a] * v * pi[a];
+    for (int a = 0; a < TM; ++a) {
+      if (a >= ti || (diag && a > b)) continue;
+      const int slot = diag ? a * tj - (a * (a - 1)) / 2 + (b - a) : a * tj + b;
+      R v[VEC];
+      vload<R, VEC>(V + (long long)slot * n3 + r, v);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        ai[a][e] += fb * v[e] * pb[e];
+        if (!(diag && a == b)) aj[e] += fi[a] * v[e] * pi[a][e];
       }
     }
     if (diag) {
+      // J side of a diagonal tile is the I side: fold into ai[b]
 #pragma unroll
-      for (int a = 0; a < TM; ++a)
-        if (a < ti) vx[(long long)(i0 + a) * n3 + r] += c * ((double)ai[a] + (double)aj[a]);
+      for (int e = 0; e < VEC; ++e) ai[b][e] += aj[e];
     } else {
-#pragma unroll
-      for (int a = 0; a < TM; ++a)
-        if (a < ti) vx[(long long)(i0 + a) * n3 + r] += c * (double)ai[a];
-#pragma unroll
-      for (int b = 0; b < TM; ++b)
-        if (b < tj) vx[(long long)(j0 + b) * n3 + r] += c * (double)aj[b];
+      vacc<R, VEC>(vx + (long long)(j0 + b) * n3 + r, c, aj);
     }
   }
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+    if (a < ti) vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, c, ai[a]);
 }
 
 }  // namespace exx

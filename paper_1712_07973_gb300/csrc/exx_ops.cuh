@@ -24,55 +24,73 @@ struct Ops {
   void (*inv_yx)(const void* X3, void* V, const void* tw, int npair, cudaStream_t st) = nullptr;
 };
 
-constexpr size_t kSmemBudget = 227 * 1024 - 1024;  // per CTA, minus static shared
+constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation of one CTA
 
-// largest batch (<= 16 lines) whose scratch fits next to the slab
-constexpr int choose_q(size_t fixed, size_t per) {
-  if (fixed >= kSmemBudget) return 0;
-  size_t q = (kSmemBudget - fixed) / per;
-  return q > 16 ? 16 : (int)q;
+// Launch shape of the slab kernels (fwd_xy, inv_yx): shared memory = fixed
+// part (slab + twiddles) + Q scratch rows.  Two CTAs of 320 threads per SM
+// when at least 8 rows of scratch fit in half an SM, else one CTA of 640.
+struct SlabShape {
+  int q, nt, minb;
+  size_t smem;
+};
+constexpr SlabShape slab_shape(size_t fixed, size_t line) {
+  const size_t half = 113 * 1024;
+  if (fixed + 8 * line <= half) {
+    size_t q = (half - fixed) / line;
+    q = q > 32 ? 32 : q;
+    return SlabShape{(int)q, 320, 2, fixed + q * line};
+  }
+  if (fixed + line > kSmemPerCTA) return SlabShape{0, 0, 0, 0};
+  size_t q = (kSmemPerCTA - fixed) / line;
+  q = q > 64 ? 64 : q;
+  return SlabShape{(int)q, 640, 1, fixed + q * line};
+}
+// zconv warps: a count that divides the L2-long passes when possible
+constexpr int zconv_warps(int l2) {
+  return (l2 % 8 == 0) ? 8 : (l2 % 6 == 0) ? 6 : (l2 % 7 == 0) ? 7 : (l2 % 5 == 0) ? 5 : 4;
 }
 
 template <typename R, int N> struct OpsImpl {
   using C = cplx<R>;
   static constexpr int L = 2 * N;
   static constexpr int L1 = split_l1(L);
-  static constexpr int L2 = L1 ? L / L1 : 0;
-  static constexpr int NT = 256;
-  static constexpr int NW = 4;
+  static constexpr int L2 = L1 ? L / L1 : 1;
+  static constexpr int X1 = split_x(N);
+  static constexpr size_t slab = (size_t)(N + 1) * (N + 1) * sizeof(C);
+  static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
+  static constexpr SlabShape SA = slab_shape(slab + (size_t)2 * L * sizeof(C), line);
+  static constexpr SlabShape SC = slab_shape(slab + (size_t)L * sizeof(C), line);
+  static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb;
+  static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb;
+  static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
+  static constexpr int NW = zconv_warps(L2);
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
-  static constexpr size_t slab = (size_t)(N + 1) * N * sizeof(C) + (size_t)L * sizeof(C);
-  static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
-  static constexpr int QA = L1 ? choose_q(slab, line + 2 * N * sizeof(R)) : 0;
-  static constexpr int QC = L1 ? choose_q(slab, line) : 0;
-  static constexpr bool ok = L1 != 0 && QA >= 1 && QC >= 1;
-  static constexpr size_t smem_a = slab + QA * line + 2 * QA * N * sizeof(R);
-  static constexpr size_t smem_b = (size_t)L * sizeof(C) + (size_t)L * W * sizeof(C);
-  static constexpr size_t smem_c = slab + QC * line;
+  static constexpr size_t smem_b = ((size_t)2 * L + (size_t)L * W) * sizeof(C);
+  static constexpr bool ok = L1 != 0 && X1 != 0 && QA >= 1 && QC >= 1 && smem_b <= kSmemPerCTA;
 
   static cudaError_t setup() {
     if constexpr (ok) {
       cudaError_t e;
-      e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT, QA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_a);
+      e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_b);
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_b);
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      return cudaFuncSetAttribute(k_inv_yx<R, N, NT, QC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_c);
+      return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
     }
     return cudaErrorNotSupported;
   }
-  static void fwd_xy(const void* psi, const int4* pairs, int npair, void* X2, const void* tw,
+  static void fwd_xy(const void* psi, const int4* pairs, int npair, void* X, const void* tw,
                      long long n3, cudaStream_t st) {
     if constexpr (ok)
-      k_fwd_xy<R, N, NT, QA><<<dim3(N, npair), NT, smem_a, st>>>(
-          static_cast<const R*>(psi), pairs, static_cast<C*>(X2), static_cast<const C*>(tw), n3);
+      k_fwd_xy<R, N, NT_A, MINB_A, QA><<<dim3(N, npair), NT_A, smem_a, st>>>(
+          static_cast<const R*>(psi), pairs, static_cast<C*>(X), static_cast<const C*>(tw), n3);
   }
   static void zconv(void* X, const void* Gs, const void* tw, double* epart, int npair,
                     bool energy_only, cudaStream_t st) {
@@ -86,18 +104,18 @@ template <typename R, int N> struct OpsImpl {
             static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
     }
   }
-  static void inv_yx(const void* X3, void* V, const void* tw, int npair, cudaStream_t st) {
+  static void inv_yx(const void* X, void* V, const void* tw, int npair, cudaStream_t st) {
     if constexpr (ok)
-      k_inv_yx<R, N, NT, QC><<<dim3(N, npair), NT, smem_c, st>>>(
-          static_cast<const C*>(X3), static_cast<R*>(V), static_cast<const C*>(tw));
+      k_inv_yx<R, N, NT_C, MINB_C, QC><<<dim3(N, npair), NT_C, smem_c, st>>>(
+          static_cast<const C*>(X), static_cast<R*>(V), static_cast<const C*>(tw));
   }
   static Ops make() {
     Ops o;
     o.n = N;
     o.supported = ok;
     o.nyb = NYB;
-    o.nt_a = NT;
-    o.nt_c = NT;
+    o.nt_a = NT_A;
+    o.nt_c = NT_C;
     o.nw_b = NW;
     o.smem_a = smem_a;
     o.smem_b = smem_b;

@@ -42,6 +42,11 @@ EXPORTS = {
     "exx_plan_info": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, _c_size_p, _c_int_p,
                                      _c_int_p]),
     "exx_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "exx_apply_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _c_double_p,
+                                      ctypes.c_void_p]),
+    "exx_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "exx_profile_read": (ctypes.c_int, [ctypes.c_void_p, _c_double_p,
+                                        ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "exx_kernel_spectrum": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _c_double_p]),
     "exx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "exx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -90,6 +95,14 @@ def kernel_spectrum(n, h, kind=KERNEL_SINC):
     _check(load_library().exx_kernel_spectrum(n, float(h), int(kind),
                                               out.ctypes.data_as(_c_double_p)), "exx_kernel_spectrum")
     return out.reshape(n + 1, n + 1, n + 1)
+
+
+def _host_ptr(a):
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if a.is_cuda:
+        raise ExxError(1, "host buffer", "a host tensor is required")
+    return a.data_ptr()
 
 
 def _stream_ptr(stream):
@@ -179,6 +192,27 @@ class ExxPlan:
         _check(self.lib.exx_pair_energies(self.handle, out.ctypes.data_as(_c_double_p),
                                           _stream_ptr(stream)), "exx_pair_energies", self.handle)
         return out
+
+    def apply_host(self, psi_host, vx_host, stream=None):
+        """exx_apply_host on (page-locked) host tensors/arrays; returns E_x."""
+        E = ctypes.c_double()
+        _check(self.lib.exx_apply_host(self.handle, ctypes.c_void_p(_host_ptr(psi_host)),
+                                       ctypes.c_void_p(_host_ptr(vx_host)), ctypes.byref(E),
+                                       _stream_ptr(stream)), "exx_apply_host", self.handle)
+        return E.value
+
+    KINDS = ("fwd_xy", "zconv", "pair_energy", "inv_yx", "accum", "exx_total", "to_float")
+
+    def profile(self, enable=True):
+        _check(self.lib.exx_profile_enable(self.handle, int(bool(enable))), "exx_profile_enable")
+
+    def profile_read(self, reset=True):
+        """Summed ms and launch counts per kernel kind since the last reset."""
+        ms = (ctypes.c_double * len(self.KINDS))()
+        cnt = (ctypes.c_longlong * len(self.KINDS))()
+        _check(self.lib.exx_profile_read(self.handle, ms, cnt, int(bool(reset))),
+               "exx_profile_read", self.handle)
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KINDS)}
 
     def info(self):
         t, nt, la, le = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -207,3 +207,24 @@ def test_fp32_workload_64_orbitals_n96_full_size(torch_dev):
     assert np.max(np.abs(samples - ref)) <= 2e-6 * max(np.max(np.abs(ref)), scale)
     norms = np.array([r.h ** 3 * np.sum(v.astype(np.float64) ** 2) for v in vx])
     assert np.allclose(norms, g["vx_norm2"], rtol=1e-5)
+
+
+def test_misaligned_caller_pointers(torch_dev):
+    # orbitals and output that start 4 bytes past an aligned address take the
+    # scalar path of the accumulation and must give the same result
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    psi = _orbitals(8, 3, seed=31)
+    occ = np.array([2.0, 1.0, 2.0])
+    plan = exx.ExxPlan(8, 0.45, 0.25, occ, precision="fp32")
+    base = torch.from_numpy(psi.astype(np.float32)).to(dev)
+    E0, v0 = plan.apply(base)
+    buf = torch.zeros(base.numel() + 1, dtype=torch.float32, device=dev)
+    buf[1:] = base.reshape(-1)
+    shifted = buf[1:].view(base.shape)
+    outbuf = torch.zeros(base.numel() + 1, dtype=torch.float32, device=dev)
+    out = outbuf[1:].view(base.shape)
+    E1, v1 = plan.apply(shifted, out)
+    assert E1 == E0
+    assert torch.allclose(v1, v0, rtol=0, atol=1e-6 * float(v0.abs().max()))
+    plan.close()
