@@ -163,6 +163,33 @@ exx_status_t exx_apply_host(exx_plan_t plan, const void* psi_host, void* vxpsi_h
 exx_status_t exx_profile_enable(exx_plan_t plan, int enable);
 exx_status_t exx_profile_read(exx_plan_t plan, double* ms, long long* launches, int reset);
 
+/*
+ * exx_pair_energy_noalloc -- E_ij = h^3 sum_r rho_ij V_ij of one orbital pair
+ * (FP32 path, same kernels as exx_energy) without a plan and without
+ * allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as codes that
+ * give the whole device memory to their own pool allocator at start-up, or
+ * that must keep allocation latency and its implicit synchronisation out of
+ * their iteration loop.
+ *   n, h, kernel   grid points per axis (2 <= n <= EXX_NOALLOC_MAX_N), spacing,
+ *                  exx_kernel_t.
+ *   psi            device, float [norb][n][n][n]; orbitals i and j are used.
+ *   E_dev          device, one double, receives E_ij (no host copy, no sync).
+ * Scratch is a set of file-scope device arrays sized for EXX_NOALLOC_MAX_N
+ * (about 18 MB, held by every GPU that loads the library until the process
+ * exits).  n > EXX_NOALLOC_MAX_N returns EXX_ERR_NOT_SUPPORTED, as does a grid
+ * without compiled kernels.  The first call on a device looks up the arrays'
+ * device addresses (cudaGetSymbolAddress), and any call whose (n, h, kernel)
+ * differs from the previous one on that device builds the kernel spectrum on
+ * the host, copies it in and synchronises the stream: make such calls before
+ * any stream capture.  All calls on a device share the arrays, which keep the
+ * last call's contents; calls that overlap on the GPU race and must be
+ * serialised by the caller (one stream, or events).
+ */
+#define EXX_NOALLOC_MAX_N 96
+exx_status_t exx_pair_energy_noalloc(int n, double h, int kernel, const float* psi, int norb,
+                                     int i, int j, double* E_dev, void* cuda_stream);
+
 /* exx_plan_destroy -- free the plan and its device memory (NULL is a no-op). */
 exx_status_t exx_plan_destroy(exx_plan_t plan);
 

@@ -46,6 +46,8 @@ static const Ops* lookup_ops(int prec, int n) {
   }
 }
 
+const Ops* find_ops(int prec, int n) { return lookup_ops(prec, n); }
+
 // ------------------------------------------------------ pair enumeration
 // Global pair id of (i, j), i <= j, in row-major order over the upper
 // triangle: g(i, j) = i N - i (i - 1) / 2 + (j - i).

@@ -1,0 +1,173 @@
+// Allocation-free pair energy (exx_pair_energy_noalloc, declared in
+// include/exx.h).
+//
+// Some callers cannot call cudaMalloc: host codes that hand the whole device
+// memory to their own pool allocator at start-up and forbid any other
+// allocation, and codes that must not take the implicit device-wide
+// synchronisation and latency an allocation can bring inside their iteration
+// loop.  This entry point serves them: it runs the energy-only path of one
+// orbital pair (co-density + x/y transforms, z transforms with the kernel
+// multiply and Parseval sum, block reduction) on scratch that lives in the
+// file-scope device arrays below, and never allocates device memory.
+//
+// The arrays are sized for grids up to EXX_NOALLOC_MAX_N points per axis
+// (about 18 MB in total); every GPU that loads the library keeps them until
+// the process exits.  In host code an array's name is only a host-side
+// stand-in, so the device addresses are looked up once per device with
+// cudaGetSymbolAddress and passed to the kernels as plain pointers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "../../include/exx.h"
+#include "exx_ops.cuh"
+
+namespace exx_host {
+bool kernel_spectrum_octant(int n, double h, int kind, double* out);
+}
+namespace exx {
+const Ops* find_ops(int prec, int n);
+}
+
+constexpr int kNoallocMaxN = EXX_NOALLOC_MAX_N;
+constexpr size_t kSpecElems = (size_t)(kNoallocMaxN + 1) * kNoallocMaxN * 2 * kNoallocMaxN;
+constexpr size_t kKernElems =
+    (size_t)(kNoallocMaxN + 1) * (kNoallocMaxN + 1) * (kNoallocMaxN + 1);
+constexpr int kTwElems = 4 * kNoallocMaxN;  // 2n high + 2n low twiddle parts
+constexpr int kEpartElems = (kNoallocMaxN + 1) * ((2 * kNoallocMaxN + 31) / 32);
+
+// Shared scratch of every call on a device (contents persist between calls):
+// the pair's spectrum (complex), the scaled kernel octant, the twiddles, the
+// column-block energy partials and the pair slot.
+static __device__ __align__(256) float2 g_noalloc_spec[kSpecElems];
+static __device__ __align__(256) float g_noalloc_kern[kKernElems];
+static __device__ __align__(256) float2 g_noalloc_tw[kTwElems];
+static __device__ __align__(256) double g_noalloc_epart[kEpartElems];
+static __device__ __align__(256) int4 g_noalloc_pair[1];
+
+namespace {
+
+constexpr int kMaxN = kNoallocMaxN;
+
+// Per-device addresses of the arrays and the (n, h, kernel) whose spectrum and
+// twiddles they currently hold.
+struct DeviceScratch {
+  bool ready = false;
+  float2* spec = nullptr;
+  float* kern = nullptr;
+  float2* tw = nullptr;
+  double* epart = nullptr;
+  int4* pair = nullptr;
+  int n = 0;
+  double h = 0.0;
+  int kind = -1;
+};
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+DeviceScratch g_noalloc_dev[kMaxDevices];
+
+__global__ void k_noalloc_set_pair(int i, int j) { g_noalloc_pair[0] = make_int4(i, j, 0, 0); }
+
+// E = h^3 * (sum of the column-block partials), fixed-order warp reduction
+__global__ void k_noalloc_pair_total(const double* __restrict__ epart, int nper, double h3,
+                                     double* __restrict__ E) {
+  double s = 0.0;
+  for (int t = threadIdx.x; t < nper; t += 32) s += epart[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) *E = h3 * s;
+}
+
+// One-time set-up on the current device: device addresses of the arrays.
+exx_status_t lookup_addresses(DeviceScratch& d) {
+  if (cudaGetSymbolAddress(reinterpret_cast<void**>(&d.spec), g_noalloc_spec) != cudaSuccess ||
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&d.kern), g_noalloc_kern) != cudaSuccess ||
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&d.tw), g_noalloc_tw) != cudaSuccess ||
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&d.epart), g_noalloc_epart) != cudaSuccess ||
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&d.pair), g_noalloc_pair) != cudaSuccess) {
+    cudaGetLastError();
+    return EXX_ERR_CUDA;
+  }
+  d.ready = true;
+  return EXX_OK;
+}
+
+// Kernel spectrum (scaled by 1/(2n)^3, FP32) and twiddles for (n, h, kind),
+// built on the host and copied into the arrays; synchronises the stream.
+exx_status_t load_tables(DeviceScratch& d, const exx::Ops* ops, int n, double h, int kind,
+                         cudaStream_t st) {
+  const size_t m = (size_t)n + 1;
+  std::vector<double> G(m * m * m);
+  if (!exx_host::kernel_spectrum_octant(n, h, kind, G.data())) return EXX_ERR_INVALID_ARG;
+  const double L = 2.0 * n;
+  const double scale = 1.0 / (L * L * L);
+  std::vector<float> Gf(G.size());
+  for (size_t k = 0; k < G.size(); ++k) Gf[k] = (float)(G[k] * scale);
+  std::vector<float2> tw(4 * (size_t)n);
+  for (int k = 0; k < 2 * n; ++k) {
+    const double a = -M_PI * (double)k / (double)n;
+    const double c = std::cos(a), s = std::sin(a);
+    tw[k] = make_float2((float)c, (float)s);
+    tw[2 * n + k] = make_float2((float)(c - (double)(float)c), (float)(s - (double)(float)s));
+  }
+  cudaError_t e = cudaMemcpyAsync(d.kern, Gf.data(), Gf.size() * sizeof(float),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = ops->setup();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    d.kind = -1;
+    return EXX_ERR_CUDA;
+  }
+  d.n = n;
+  d.h = h;
+  d.kind = kind;
+  return EXX_OK;
+}
+
+}  // namespace
+
+extern "C" exx_status_t exx_pair_energy_noalloc(int n, double h, int kernel, const float* psi,
+                                                int norb, int i, int j, double* E_dev,
+                                                void* cuda_stream) {
+  if (psi == nullptr || E_dev == nullptr || norb < 1 || i < 0 || j < 0 || i >= norb ||
+      j >= norb || n < 2 || !(h > 0.0) || !std::isfinite(h))
+    return EXX_ERR_INVALID_ARG;
+  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY) return EXX_ERR_INVALID_ARG;
+  if (n > kMaxN) return EXX_ERR_NOT_SUPPORTED;  // beyond the static scratch
+  const exx::Ops* ops = exx::find_ops(EXX_FP32, n);
+  if (ops == nullptr || !ops->supported) return EXX_ERR_NOT_SUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return EXX_ERR_CUDA;
+  }
+  DeviceScratch* d = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    d = &g_noalloc_dev[dev];
+    if (!d->ready) {
+      const exx_status_t s = lookup_addresses(*d);
+      if (s != EXX_OK) return s;
+    }
+    if (d->n != n || d->h != h || d->kind != kernel) {
+      const exx_status_t s = load_tables(*d, ops, n, h, kernel, st);
+      if (s != EXX_OK) return s;
+    }
+  }
+  // Every scratch element read below is first written by this call (the pair
+  // slot, the n-sized part of the spectrum, the column-block partials), so
+  // nothing needs clearing.
+  const long long n3 = (long long)n * n * n;
+  k_noalloc_set_pair<<<1, 1, 0, st>>>(i, j);
+  ops->fwd_xy(psi, d->pair, 1, d->spec, d->tw, n3, st);
+  ops->zconv(d->spec, d->kern, d->tw, d->epart, 1, true, st);
+  k_noalloc_pair_total<<<1, 32, 0, st>>>(d->epart, (n + 1) * ops->nyb, h * h * h, E_dev);
+  if (cudaGetLastError() != cudaSuccess) return EXX_ERR_CUDA;
+  return EXX_OK;
+}

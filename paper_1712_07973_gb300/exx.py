@@ -48,6 +48,9 @@ EXPORTS = {
     "exx_profile_read": (ctypes.c_int, [ctypes.c_void_p, _c_double_p,
                                         ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "exx_kernel_spectrum": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _c_double_p]),
+    "exx_pair_energy_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "exx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "exx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "exx_version": (ctypes.c_char_p, []),
