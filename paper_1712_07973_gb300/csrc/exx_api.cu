@@ -439,10 +439,9 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
       }
       ProfScope ps(p, K_ACCUM, st);
       const int threads = 256;
-      // vector width: 4 floats / 2 doubles per thread when n^3 and the
-      // caller's pointers allow aligned vector accesses
+      // vector width: 2 values per thread when n^3 and the caller's pointers
+      // allow aligned vector accesses
       const bool al = ((uintptr_t)psi % 16 == 0) && ((uintptr_t)acc % 16 == 0);
-      const bool v4 = al && (n3 % 4) == 0;
       const bool v2 = al && (n3 % 2) == 0;
       if (p->prec == EXX_FP64) {
         const int vec = v2 ? 2 : 1;
@@ -456,10 +455,10 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
               static_cast<const double*>(psi), static_cast<const double*>(p->V), acc, p->d_occ,
               t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
       } else {
-        const int vec = v4 ? 4 : 1;
+        const int vec = v2 ? 2 : 1;
         const long long blocks = (n3 / vec + threads - 1) / threads;
-        if (v4)
-          k_accum<float, 8, 4><<<(unsigned)blocks, threads, 0, st>>>(
+        if (v2)
+          k_accum<float, 8, 2><<<(unsigned)blocks, threads, 0, st>>>(
               static_cast<const float*>(psi), static_cast<const float*>(p->V), acc, p->d_occ,
               t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
         else

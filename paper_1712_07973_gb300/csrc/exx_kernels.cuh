@@ -141,8 +141,10 @@ k_fwd_xy(const R* __restrict__ psi, const int4* __restrict__ pairs, cplx<R>* __r
   C* S = Sl + (N + 1) * SP;
   for (int r0 = 0; r0 <= N; r0 += Q) {
     const int nr = min(Q, N + 1 - r0);
+    // units (kx row, n2) with the row fastest: the slab reads stride SP and the
+    // scratch writes stride the (odd) line length, both bank-conflict free
     for (int u = tid; u < nr * L2; u += NT) {
-      const int r = u / L2, n2 = u - r * L2;
+      const int n2 = u / nr, r = u - n2 * nr;
       const C* row = Sl + (r0 + r) * SP;
       C v[L1];
 #pragma unroll
@@ -315,8 +317,8 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
       for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], tw[m2 * k1]);
     }
     __syncthreads();
-    for (int u = tid; u < nr * L2; u += NT) {
-      const int r = u / L2, m2 = u - r * L2;
+    for (int u = tid; u < nr * L2; u += NT) {  // row fastest (see fwd_xy)
+      const int m2 = u / nr, r = u - m2 * nr;
       const C* q = S + r * Scr<L1, L2>::line + m2 * Scr<L1, L2>::row;
       C v[L1];
 #pragma unroll
@@ -386,6 +388,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
 // only the I-side partial sums stay live.
 template <typename R, int VEC> struct vecty;
 template <> struct vecty<float, 4> { using type = float4; };
+template <> struct vecty<float, 2> { using type = float2; };
 template <> struct vecty<float, 1> { using type = float; };
 template <> struct vecty<double, 2> { using type = double2; };
 template <> struct vecty<double, 1> { using type = double; };
@@ -426,7 +429,7 @@ __device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
 }
 
 template <typename R, int TM, int VEC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
 k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__ vx,
         const double* __restrict__ occ, int i0, int ti, int j0, int tj, int diag, double c,
         long long n3) {
