@@ -342,6 +342,27 @@ def run_ours(a):
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8,
                    "api": "exx_apply_host"}
 
+    # autograd path: forward + hand-written backward through ExxEnergy (the
+    # backward is the exchange action computed in the same pair solves)
+    from paper_1712_07973_gb300 import autograd as ag
+    pg = psi.clone().requires_grad_(True)
+    for _ in range(2):
+        pg.grad = None
+        ag.exx_energy(pg, plan).backward()
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    ag_steps = max(3, min(a.steps, 10))
+    a0.record(stream)
+    for _ in range(ag_steps):
+        pg.grad = None
+        ag.exx_energy(pg, plan).backward()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    line["autograd"] = {"ms_per_step": a0.elapsed_time(a1) / ag_steps,
+                        "what": "E_x forward + gradient backward via torch.autograd"}
+    del pg
+
     # FP64 plain GPU path on the same workload (the comparison the metric names)
     if not a.no_fp64:
         p64 = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp64")
