@@ -190,6 +190,73 @@ exx_status_t exx_profile_read(exx_plan_t plan, double* ms, long long* launches, 
 exx_status_t exx_pair_energy_noalloc(int n, double h, int kernel, const float* psi, int norb,
                                      int i, int j, double* E_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched, uneven workloads: many independent molecules (each with its own
+ * grid n, spacing, alpha, occupations and orbital count) in one call.
+ * Molecules that share (n, h) share the kernel spectrum and every launch of
+ * the pipeline; their pair tiles are scheduled in waves that take at most one
+ * tile of each molecule, so each molecule's accumulation order, and result,
+ * equals that of its own exx_plan with the same tile edge.  FP32 path only
+ * (psi and vxpsi are float; kernel, energies and accumulation in FP64).
+ * ------------------------------------------------------------------------ */
+typedef struct exx_batch_s* exx_batch_t;
+
+typedef struct {
+  int n;                      /* grid points per axis (cubic)                  */
+  double h;                   /* grid spacing, bohr                            */
+  double alpha;               /* exact-exchange fraction                       */
+  const double* occupations;  /* host, norb values; copied at creation         */
+  int norb;                   /* orbitals                                      */
+  int tile;                   /* pair-tile edge 1..8 (0: default 8)            */
+} exx_mol_desc;
+
+/*
+ * exx_batch_create -- plan a batch of nmol molecules (mols: host array).
+ * kernel: exx_kernel_t.  Allocates the workspace of the largest wave (waves
+ * hold at most 512 pair solves) and one FP64 accumulator per molecule.
+ */
+exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mols, int kernel,
+                              void* cuda_stream);
+
+/*
+ * exx_batch_set_buffers -- bind the orbital and output arrays: psi, vxpsi are
+ * host arrays of nmol device pointers (float [norb_m][n_m]^3 each); vxpsi may
+ * be NULL for energy-only use.  The pointers are copied into device tables
+ * that later calls (and captured graphs) read, so rebinding does not require
+ * a new capture.  Synchronises the stream.
+ */
+exx_status_t exx_batch_set_buffers(exx_batch_t batch, const float* const* psi,
+                                   float* const* vxpsi, void* cuda_stream);
+
+/*
+ * exx_batch_apply / exx_batch_energy -- E_x of every molecule into E_dev
+ * (device, nmol doubles) and, for apply, Vx psi into the bound outputs.
+ * Asynchronous on the stream.
+ */
+exx_status_t exx_batch_apply(exx_batch_t batch, double* E_dev, void* cuda_stream);
+exx_status_t exx_batch_energy(exx_batch_t batch, double* E_dev, void* cuda_stream);
+
+/*
+ * exx_batch_graph -- enable (1) or disable (0) CUDA-graph execution: the next
+ * apply (or energy) call captures its whole enqueue sequence on the given
+ * stream (which must be a created stream, not the legacy default stream) and
+ * launches the graph; later calls with the same stream and E_dev relaunch it.
+ */
+exx_status_t exx_batch_graph(exx_batch_t batch, int enable);
+
+/* exx_batch_pair_energies -- pair energies of molecule mol (order as in
+ * exx_pair_energies) of the last call, to host memory; synchronises. */
+exx_status_t exx_batch_pair_energies(exx_batch_t batch, int mol, double* out_host,
+                                     void* cuda_stream);
+
+/* exx_batch_info -- (n, h) groups, waves, device workspace bytes, kernel
+ * launches of one apply, total pair solves (each out-parameter may be NULL). */
+exx_status_t exx_batch_info(exx_batch_t batch, int* ngroups, int* nwaves, size_t* workspace_bytes,
+                            int* launches_apply, long long* pairs);
+
+/* exx_batch_destroy -- free the batch (NULL is a no-op). */
+exx_status_t exx_batch_destroy(exx_batch_t batch);
+
 /* exx_plan_destroy -- free the plan and its device memory (NULL is a no-op). */
 exx_status_t exx_plan_destroy(exx_plan_t plan);
 

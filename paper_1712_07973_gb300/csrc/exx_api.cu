@@ -28,7 +28,7 @@ namespace exx {
 // ---------------------------------------------------------------- registry
 #define EXX_SIZES(X)                                                                         \
   X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(16) X(18) X(20) X(24) X(28)    \
-  X(32) X(36) X(40) X(48) X(56) X(64) X(72) X(80) X(96) X(112) X(128)
+  X(32) X(36) X(40) X(48) X(56) X(64) X(72) X(80) X(96) X(112) X(128) X(160)
 
 #define EXX_DECL(N) const Ops* ops_f32_##N(); const Ops* ops_f64_##N();
 EXX_SIZES(EXX_DECL)
@@ -421,7 +421,7 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
     const int4* pr = p->d_pairs + t.off;
     {
       ProfScope ps(p, K_FWD, st);
-      p->ops->fwd_xy(psi, pr, t.count, p->X2, p->tw, n3, st);
+      p->ops->fwd_xy(psi, nullptr, pr, t.count, p->X2, p->tw, n3, st);
     }
     {
       ProfScope ps(p, K_ZCONV, st);

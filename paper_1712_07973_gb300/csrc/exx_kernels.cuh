@@ -55,8 +55,9 @@ template <typename R> __device__ __forceinline__ R sq(R a) { return a * a; }
 // pruned length-2n FFT per kx row, written to HBM as X[p][kx][z][ky].
 template <typename R, int N, int NT, int MINB, int Q>
 __global__ void __launch_bounds__(NT, MINB)
-k_fwd_xy(const R* __restrict__ psi, const int4* __restrict__ pairs, cplx<R>* __restrict__ X,
-         const cplx<R>* __restrict__ tw_g, long long n3) {
+k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
+         const int4* __restrict__ pairs, cplx<R>* __restrict__ X, const cplx<R>* __restrict__ tw_g,
+         long long n3) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int X1 = split_x(N), X2 = N / X1;
@@ -71,7 +72,8 @@ k_fwd_xy(const R* __restrict__ psi, const int4* __restrict__ pairs, cplx<R>* __r
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
   const int p = blockIdx.y;
-  const int4 pr = pairs[p];
+  const int4 pr = pairs[p];  // (i, j, pair id, molecule slot)
+  const R* psi = psi_tab ? psi_tab[pr.w] : psi0;
   const R* __restrict__ pi = psi + (long long)pr.x * n3 + (long long)z * N * N;
   const R* __restrict__ pj = psi + (long long)pr.y * n3 + (long long)z * N * N;
   for (int t = tid; t < 2 * L; t += NT) tw[t] = tw_g[t];
@@ -481,6 +483,77 @@ k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__
 #pragma unroll
   for (int a = 0; a < TM; ++a)
     if (a < ti) vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, c, ai[a]);
+}
+
+// Tile descriptor of a batched wave (tiles of different molecules, or of
+// disjoint orbital blocks, so that no two touch the same accumulator).
+struct TileDesc {
+  int i0, ti, j0, tj, diag;
+  int voff;   // first pair slot of the tile in V
+  int mol;    // molecule slot: psi_tab[mol], vx_tab[mol], occ + occ_off[mol]
+  int occ_off;
+  double c;   // -alpha of the molecule
+};
+
+template <typename R, int TM, int VEC>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
+k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
+              double* const* __restrict__ vx_tab, const double* __restrict__ occ,
+              const TileDesc* __restrict__ tiles, long long n3) {
+  const TileDesc t = tiles[blockIdx.y];
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
+  if (r >= n3) return;
+  const R* __restrict__ psi = psi_tab[t.mol];
+  double* __restrict__ vx = vx_tab[t.mol];
+  const double* __restrict__ oc = occ + t.occ_off;
+  const R* __restrict__ Vt = V + (long long)t.voff * n3;
+  const int ti = t.ti, tj = t.tj, i0 = t.i0, j0 = t.j0;
+  const bool diag = t.diag != 0;
+  R fi[TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a) fi[a] = a < ti ? (R)oc[i0 + a] : R(0);
+  R pi[TM][VEC], ai[TM][VEC];
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    if (a < ti) vload<R, VEC>(psi + (long long)(i0 + a) * n3 + r, pi[a]);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) ai[a][e] = R(0);
+  }
+#pragma unroll
+  for (int b = 0; b < TM; ++b) {
+    if (b >= tj) break;
+    const R fb = (R)oc[j0 + b];
+    R pb[VEC], aj[VEC];
+    if (diag) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) pb[e] = pi[b][e];
+    } else {
+      vload<R, VEC>(psi + (long long)(j0 + b) * n3 + r, pb);
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) aj[e] = R(0);
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+      if (a >= ti || (diag && a > b)) continue;
+      const int slot = diag ? a * tj - (a * (a - 1)) / 2 + (b - a) : a * tj + b;
+      R v[VEC];
+      vload<R, VEC>(Vt + (long long)slot * n3 + r, v);
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) {
+        ai[a][e] += fb * v[e] * pb[e];
+        if (!(diag && a == b)) aj[e] += fi[a] * v[e] * pi[a][e];
+      }
+    }
+    if (diag) {
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) ai[b][e] += aj[e];
+    } else {
+      vacc<R, VEC>(vx + (long long)(j0 + b) * n3 + r, t.c, aj);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+    if (a < ti) vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, t.c, ai[a]);
 }
 
 }  // namespace exx

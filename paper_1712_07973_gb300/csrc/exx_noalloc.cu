@@ -165,7 +165,7 @@ extern "C" exx_status_t exx_pair_energy_noalloc(int n, double h, int kernel, con
   // nothing needs clearing.
   const long long n3 = (long long)n * n * n;
   k_noalloc_set_pair<<<1, 1, 0, st>>>(i, j);
-  ops->fwd_xy(psi, d->pair, 1, d->spec, d->tw, n3, st);
+  ops->fwd_xy(psi, nullptr, d->pair, 1, d->spec, d->tw, n3, st);
   ops->zconv(d->spec, d->kern, d->tw, d->epart, 1, true, st);
   k_noalloc_pair_total<<<1, 32, 0, st>>>(d->epart, (n + 1) * ops->nyb, h * h * h, E_dev);
   if (cudaGetLastError() != cudaSuccess) return EXX_ERR_CUDA;

@@ -17,8 +17,10 @@ struct Ops {
   int nw_b = 0;            // warps per CTA of zconv
   size_t smem_a = 0, smem_b = 0, smem_c = 0;
   cudaError_t (*setup)() = nullptr;
-  void (*fwd_xy)(const void* psi, const int4* pairs, int npair, void* X2, const void* tw,
-                 long long n3, cudaStream_t st) = nullptr;
+  // psi_tab (device array of orbital-array pointers, indexed by the pair's
+  // molecule slot) may be null, in which case every pair reads psi
+  void (*fwd_xy)(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
+                 void* X, const void* tw, long long n3, cudaStream_t st) = nullptr;
   void (*zconv)(void* X, const void* Gs, const void* tw, double* epart, int npair,
                 bool energy_only, cudaStream_t st) = nullptr;
   void (*inv_yx)(const void* X3, void* V, const void* tw, int npair, cudaStream_t st) = nullptr;
@@ -86,11 +88,12 @@ template <typename R, int N> struct OpsImpl {
     }
     return cudaErrorNotSupported;
   }
-  static void fwd_xy(const void* psi, const int4* pairs, int npair, void* X, const void* tw,
-                     long long n3, cudaStream_t st) {
+  static void fwd_xy(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
+                     void* X, const void* tw, long long n3, cudaStream_t st) {
     if constexpr (ok)
       k_fwd_xy<R, N, NT_A, MINB_A, QA><<<dim3(N, npair), NT_A, smem_a, st>>>(
-          static_cast<const R*>(psi), pairs, static_cast<C*>(X), static_cast<const C*>(tw), n3);
+          static_cast<const R*>(psi), reinterpret_cast<const R* const*>(psi_tab), pairs,
+          static_cast<C*>(X), static_cast<const C*>(tw), n3);
   }
   static void zconv(void* X, const void* Gs, const void* tw, double* epart, int npair,
                     bool energy_only, cudaStream_t st) {

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["ExxError", "ExxPlan", "load_library", "kernel_spectrum", "EXPORTS",
+__all__ = ["ExxError", "ExxPlan", "ExxBatch", "load_library", "kernel_spectrum", "EXPORTS",
            "FP64", "FP32", "KERNEL_SINC", "KERNEL_HOCKNEY", "FLAG_VX_FP64"]
 
 FP64, FP32 = 0, 1
@@ -51,6 +51,18 @@ EXPORTS = {
     "exx_pair_energy_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "exx_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_void_p]),
+    "exx_batch_set_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    "exx_batch_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "exx_batch_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "exx_batch_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "exx_batch_pair_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_double_p,
+                                               ctypes.c_void_p]),
+    "exx_batch_info": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, _c_size_p, _c_int_p,
+                                      ctypes.POINTER(ctypes.c_longlong)]),
+    "exx_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "exx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "exx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "exx_version": (ctypes.c_char_p, []),
@@ -229,6 +241,106 @@ class ExxPlan:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.exx_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MolDesc(ctypes.Structure):
+    """exx_mol_desc of include/exx.h."""
+    _fields_ = [("n", ctypes.c_int), ("h", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("occupations", _c_double_p), ("norb", ctypes.c_int), ("tile", ctypes.c_int)]
+
+
+class ExxBatch:
+    """Batched FP32 exact exchange over molecules of uneven size.
+
+    mols: list of dicts with keys n, h, alpha, occupations and optional tile.
+    """
+
+    def __init__(self, mols, kernel="sinc", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise ExxError(2, "ExxBatch", "no CUDA device: the EXX operator runs only on the GPU")
+        self.lib = load_library()
+        self.nmol = len(mols)
+        self._occ = [np.ascontiguousarray(np.asarray(m["occupations"], dtype=np.float64)) for m in mols]
+        self.mols = [dict(m) for m in mols]
+        descs = (MolDesc * self.nmol)()
+        for k, m in enumerate(mols):
+            descs[k].n = int(m["n"])
+            descs[k].h = float(m["h"])
+            descs[k].alpha = float(m["alpha"])
+            descs[k].occupations = self._occ[k].ctypes.data_as(_c_double_p)
+            descs[k].norb = int(self._occ[k].size)
+            descs[k].tile = int(m.get("tile", 0))
+        handle = ctypes.c_void_p()
+        kind = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY}[kernel]
+        _check(self.lib.exx_batch_create(ctypes.byref(handle), self.nmol, ctypes.cast(descs, ctypes.c_void_p),
+                                         kind, _stream_ptr(stream)), "exx_batch_create")
+        self.handle = handle
+        self._bound = None
+
+    def set_buffers(self, psis, vxs=None, stream=None):
+        import torch
+        for k, (p, m) in enumerate(zip(psis, self.mols)):
+            n = int(m["n"])
+            if (not isinstance(p, torch.Tensor) or not p.is_cuda or p.dtype != torch.float32
+                    or not p.is_contiguous() or tuple(p.shape) != (self._occ[k].size, n, n, n)):
+                raise ExxError(1, "psi", f"molecule {k}: contiguous CUDA float32 tensor required")
+        pp = (ctypes.c_void_p * self.nmol)(*[p.data_ptr() for p in psis])
+        vv = None
+        if vxs is not None:
+            for v, p in zip(vxs, psis):
+                if v.dtype != torch.float32 or v.shape != p.shape or not v.is_contiguous() or not v.is_cuda:
+                    raise ExxError(1, "vxpsi", "contiguous CUDA float32 tensors of psi's shapes required")
+            vv = (ctypes.c_void_p * self.nmol)(*[v.data_ptr() for v in vxs])
+        _check(self.lib.exx_batch_set_buffers(self.handle, ctypes.cast(pp, ctypes.c_void_p),
+                                              ctypes.cast(vv, ctypes.c_void_p) if vv else None,
+                                              _stream_ptr(stream)), "exx_batch_set_buffers")
+        self._bound = (list(psis), list(vxs) if vxs is not None else None)
+
+    def apply(self, E_dev=None, stream=None):
+        import torch
+        if E_dev is None:
+            E_dev = torch.zeros(self.nmol, dtype=torch.float64, device="cuda")
+        _check(self.lib.exx_batch_apply(self.handle, ctypes.c_void_p(E_dev.data_ptr()),
+                                        _stream_ptr(stream)), "exx_batch_apply")
+        return E_dev
+
+    def energy(self, E_dev=None, stream=None):
+        import torch
+        if E_dev is None:
+            E_dev = torch.zeros(self.nmol, dtype=torch.float64, device="cuda")
+        _check(self.lib.exx_batch_energy(self.handle, ctypes.c_void_p(E_dev.data_ptr()),
+                                         _stream_ptr(stream)), "exx_batch_energy")
+        return E_dev
+
+    def graph(self, enable=True):
+        _check(self.lib.exx_batch_graph(self.handle, int(bool(enable))), "exx_batch_graph")
+
+    def pair_energies(self, mol, stream=None):
+        N = self._occ[mol].size
+        out = np.zeros(N * (N + 1) // 2)
+        _check(self.lib.exx_batch_pair_energies(self.handle, int(mol), out.ctypes.data_as(_c_double_p),
+                                                _stream_ptr(stream)), "exx_batch_pair_energies")
+        return out
+
+    def info(self):
+        g, w, la = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ws, pr = ctypes.c_size_t(), ctypes.c_longlong()
+        _check(self.lib.exx_batch_info(self.handle, ctypes.byref(g), ctypes.byref(w), ctypes.byref(ws),
+                                       ctypes.byref(la), ctypes.byref(pr)), "exx_batch_info")
+        return {"groups": g.value, "waves": w.value, "workspace_bytes": ws.value,
+                "launches_apply": la.value, "pairs": pr.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.exx_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -64,24 +64,24 @@ def make_orbitals(r: OrbitalRecipe, dtype=np.float64):
     rng = np.random.default_rng(r.seed)
     sites = _sites(rng, r)
     x = np.arange(r.n, dtype=np.float64) * r.h
-    phi = np.zeros((r.norb, r.n, r.n, r.n), dtype=np.float64)
+    n, G = r.n, r.gauss_per_orb
+    phi = np.empty((r.norb, n, n, n), dtype=np.float64)
     for o in range(r.norb):
-        at = rng.integers(0, r.nsites, size=r.gauss_per_orb)
-        sig = rng.uniform(r.sigma[0], r.sigma[1], size=r.gauss_per_orb)
-        coef = rng.standard_normal(r.gauss_per_orb)
-        typ = rng.integers(0, 4, size=r.gauss_per_orb) if r.p_type else np.zeros(r.gauss_per_orb, int)
-        for g in range(r.gauss_per_orb):
-            R = sites[at[g]]
-            s2 = 2.0 * sig[g] ** 2
-            dz, dy, dx = x - R[2], x - R[1], x - R[0]
-            gz, gy, gx = np.exp(-dz * dz / s2), np.exp(-dy * dy / s2), np.exp(-dx * dx / s2)
-            if typ[g] == 1:
-                gx = gx * dx
-            elif typ[g] == 2:
-                gy = gy * dy
-            elif typ[g] == 3:
-                gz = gz * dz
-            phi[o] += coef[g] * (gz[:, None, None] * gy[None, :, None] * gx[None, None, :])
+        at = rng.integers(0, r.nsites, size=G)
+        sig = rng.uniform(r.sigma[0], r.sigma[1], size=G)
+        coef = rng.standard_normal(G)
+        typ = rng.integers(0, 4, size=G) if r.p_type else np.zeros(G, int)
+        R = sites[at]                                   # (G, 3) as (x, y, z)
+        s2 = 2.0 * sig ** 2
+        dz = x[:, None] - R[None, :, 2]                 # (n, G)
+        dy = x[:, None] - R[None, :, 1]
+        dx = x[:, None] - R[None, :, 0]
+        gz = np.exp(-dz * dz / s2) * np.where(typ == 3, dz, 1.0) * coef
+        gy = np.exp(-dy * dy / s2) * np.where(typ == 2, dy, 1.0)
+        gx = np.exp(-dx * dx / s2) * np.where(typ == 1, dx, 1.0)
+        # sum over the G separable terms as one contraction: (n, G) @ (G, n^2)
+        yx = (gy[:, None, :] * gx[None, :, :]).reshape(n * n, G)
+        phi[o] = (gz @ yx.T).reshape(n, n, n)
     flat = phi.reshape(r.norb, -1)
     S = (r.h ** 3) * (flat @ flat.T)
     w, U = np.linalg.eigh(S)

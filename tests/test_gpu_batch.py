@@ -1,0 +1,155 @@
+"""GPU checks of the batched, uneven path (exx_batch_*).
+
+Each molecule's pair energies and Vx psi must equal those of its own plan
+(same kernels, same tile edge, same accumulation order; E_x to rounding, as
+its final sum runs in another order) and the FP64 oracle within the FP32
+tolerance (1e-6 Ha on E_x).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import exx_oracle as o
+from paper_1712_07973_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1712_07973_gb300 import build, exx
+    build.build()
+    return torch, torch.device("cuda:0"), exx
+
+
+def _mol(n, N, seed, h):
+    r = synth.OrbitalRecipe(n=n, h=h, norb=N, nsites=3, seed=seed, gauss_per_orb=3,
+                            sigma=(0.12 * n * h, 0.2 * n * h), p_type=True)
+    return synth.make_orbitals(r)
+
+
+SMALL = [  # (n, N, h, alpha): uneven sizes, two molecules share (n, h)
+    (8, 3, 0.45, 0.25), (12, 7, 0.4, 0.25), (12, 11, 0.4, 0.3), (16, 2, 0.35, 0.25), (10, 9, 0.5, 0.2),
+]
+
+
+def _small(env):
+    torch, dev, exx = env
+    psis, occs, mols = [], [], []
+    for k, (n, N, h, a) in enumerate(SMALL):
+        psi = _mol(n, N, 300 + k, h)
+        occ = np.linspace(0.5, 2.0, N)
+        psis.append(psi)
+        occs.append(occ)
+        mols.append({"n": n, "h": h, "alpha": a, "occupations": occ})
+    return psis, occs, mols
+
+
+def test_batch_equals_single_plans_and_oracle(env):
+    torch, dev, exx = env
+    psis, occs, mols = _small(env)
+    b = exx.ExxBatch(mols)
+    assert b.info()["groups"] == 4
+    pt = [torch.from_numpy(p).to(dev, torch.float32) for p in psis]
+    vx = [torch.empty_like(p) for p in pt]
+    b.set_buffers(pt, vx)
+    E = b.apply().cpu().numpy()
+    Ee = b.energy().cpu().numpy()
+    for k, (m, p, occ) in enumerate(zip(mols, psis, occs)):
+        plan = exx.ExxPlan(m["n"], m["h"], m["alpha"], occ, precision="fp32")
+        Es, vs = plan.apply(pt[k])
+        # the final FP64 sum runs in another order: equal to rounding
+        assert abs(E[k] - Es) <= 1e-14 * abs(Es) and abs(Ee[k] - Es) <= 1e-14 * abs(Es)
+        assert torch.equal(vx[k], vs)
+        assert np.array_equal(b.pair_energies(k), plan.pair_energies())
+        plan.close()
+        Gh = o.kernel_spectrum(o.kernel_real_space(m["n"], m["h"]))
+        Eo, vxo, _ = o.exx(p, occ, m["alpha"], m["h"], Gh)
+        assert abs(E[k] - Eo) <= 1e-6
+        assert np.max(np.abs(vx[k].double().cpu().numpy() - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+    b.close()
+
+
+def test_batch_graph_capture_replay_and_rebinding(env):
+    torch, dev, exx = env
+    psis, occs, mols = _small(env)
+    b = exx.ExxBatch(mols)
+    pt = [torch.from_numpy(p).to(dev, torch.float32) for p in psis]
+    vx = [torch.empty_like(p) for p in pt]
+    b.set_buffers(pt, vx)
+    E_ref = b.apply().clone()
+    vx_ref = [v.clone() for v in vx]
+    s = torch.cuda.Stream()
+    E = torch.zeros(len(mols), dtype=torch.float64, device=dev)
+    b.graph(True)
+    with torch.cuda.stream(s):
+        for _ in range(3):  # capture once, then replay
+            b.apply(E, stream=s)
+    s.synchronize()
+    assert torch.equal(E, E_ref)
+    assert all(torch.equal(a, c) for a, c in zip(vx, vx_ref))
+    # rebinding new orbitals (scaled by 2: E x16, Vx psi x8) reuses the graph
+    pt2 = [2.0 * p for p in pt]
+    vx2 = [torch.empty_like(p) for p in pt]
+    b.set_buffers(pt2, vx2)
+    with torch.cuda.stream(s):
+        b.apply(E, stream=s)
+    s.synchronize()
+    assert torch.allclose(E, 16.0 * E_ref, rtol=1e-6, atol=0)
+    for a, c in zip(vx2, vx_ref):
+        assert torch.allclose(a, 8.0 * c, rtol=1e-5, atol=1e-6 * float(c.abs().max()))
+    b.close()
+
+
+def test_batch_rejects_bad_descriptors(env):
+    torch, dev, exx = env
+    with pytest.raises(exx.ExxError):
+        exx.ExxBatch([{"n": 11, "h": 0.4, "alpha": 0.25, "occupations": [2.0]}])
+    with pytest.raises(exx.ExxError):
+        exx.ExxBatch([{"n": 8, "h": -0.4, "alpha": 0.25, "occupations": [2.0]}])
+    b = exx.ExxBatch([{"n": 8, "h": 0.4, "alpha": 0.25, "occupations": [2.0, 2.0]}])
+    with pytest.raises(exx.ExxError):  # no buffers bound yet
+        b.apply()
+    with pytest.raises(exx.ExxError):
+        b.set_buffers([torch.zeros((3, 8, 8, 8), device=dev)])
+    b.close()
+
+
+def test_batched_workload_16_uneven_molecules(env):
+    # 16 molecules, N_m uniform in [8, 96], grids from {48..128}^3, h = 0.4,
+    # one graph launch; every molecule equals its own plan, and a seeded sample
+    # of pair energies per molecule equals the oracle's
+    torch, dev, exx = env
+    recipes = synth.batched_workload()
+    mols, pt, occs = [], [], []
+    for r in recipes:
+        occ = np.full(r.norb, r.occupation)
+        mols.append({"n": r.n, "h": r.h, "alpha": r.alpha, "occupations": occ})
+        pt.append(torch.from_numpy(synth.make_orbitals(r, dtype=np.float32)).to(dev))
+        occs.append(occ)
+    b = exx.ExxBatch(mols)
+    vx = [torch.empty_like(p) for p in pt]
+    b.set_buffers(pt, vx)
+    b.graph(True)
+    s = torch.cuda.Stream()
+    E = torch.zeros(len(mols), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(s):
+        b.apply(E, stream=s)
+    s.synchronize()
+    rng = np.random.default_rng(4)
+    for k, (r, m) in enumerate(zip(recipes, mols)):
+        plan = exx.ExxPlan(r.n, r.h, r.alpha, occs[k], precision="fp32")
+        Es, vs = plan.apply(pt[k])
+        assert abs(float(E[k]) - Es) <= 1e-14 * abs(Es)
+        assert torch.equal(vx[k], vs)
+        Eij = plan.pair_energies()
+        plan.close()
+        Gh = o.kernel_spectrum(o.kernel_real_space(r.n, r.h))
+        pairs = o.pair_list(r.norb)
+        psi = pt[k].double().cpu().numpy()
+        for g in rng.choice(len(pairs), size=2, replace=False):
+            i, j = pairs[g]
+            _, eo = o.exx_pair(psi[i], psi[j], Gh, r.h)
+            assert abs(Eij[g] - eo) <= 1e-6 * max(1.0, abs(eo)), (k, i, j, Eij[g], eo)
+    b.close()
