@@ -46,6 +46,8 @@ def args_parse():
     ap.add_argument("--cpu-sample", type=int, default=128, help="pair solves timed on the CPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the 16-molecule batched workload (one graph launch)")
     ap.add_argument("--norb", type=int, default=0,
                     help="use only the first NORB orbitals (small profiling cases)")
     return ap.parse_args()
@@ -195,6 +197,59 @@ def cpu_oracle_rate(psi, r, npairs, seed=0):
         acc[1] += (-r.alpha * r.occupation) * V * psi[i]
     dt = time.perf_counter() - t0
     return npairs / dt, dt
+
+
+def batched_line(torch, dev, exx, synth, stream):
+    """16 molecules of uneven size (N_m in [8, 96], n_m in {48..128}^3), FP32,
+    one CUDA-graph launch per step; compared with one plan per molecule."""
+    import numpy as np
+    recipes = synth.batched_workload()
+    mols, pt = [], []
+    for r in recipes:
+        mols.append({"n": r.n, "h": r.h, "alpha": r.alpha, "occupations": np.full(r.norb, r.occupation)})
+        pt.append(torch.from_numpy(synth.make_orbitals(r, dtype=np.float32)).to(dev))
+    pairs = sum(r.norb * (r.norb + 1) // 2 for r in recipes)
+    b = exx.ExxBatch(mols)
+    vx = [torch.empty_like(p) for p in pt]
+    b.set_buffers(pt, vx)
+    b.graph(True)
+    s = torch.cuda.Stream()
+    E = torch.zeros(len(mols), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            b.apply(E, stream=s)
+        s.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        for _ in range(3):
+            b.apply(E, stream=s)
+        t1.record(s)
+    s.synchronize()
+    ms = t0.elapsed_time(t1) / 3
+    info = b.info()
+    b.close()
+    plans = [exx.ExxPlan(m["n"], m["h"], m["alpha"], m["occupations"], precision="fp32") for m in mols]
+    outs = [torch.empty_like(p) for p in pt]
+    for pl, p, o in zip(plans, pt, outs):
+        pl.apply_async(p, o)
+    torch.cuda.synchronize()
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(3):
+        for pl, p, o in zip(plans, pt, outs):
+            pl.apply_async(p, o)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = q0.elapsed_time(q1) / 3
+    for pl in plans:
+        pl.close()
+    return {"workload": "16 molecules, N_m in [8,96], n_m in {48,64,80,96,112,128}, h=0.4, seed 3",
+            "pairs": pairs, "ms_per_step": ms, "value": pairs / (ms * 1e-3), "unit": UNIT,
+            "graph": True, "groups": info["groups"], "waves": info["waves"],
+            "launches_per_step": info["launches_apply"],
+            "sequential_plans_ms": ms_seq, "speedup_vs_sequential_plans": ms_seq / ms}
 
 
 def run_reference(a):
@@ -386,6 +441,9 @@ def run_ours(a):
                 line["fp64_plain"]["E_x_abs_err_vs_oracle_Ha"] = abs(E64 - json.load(fh)["E_x"])
         p64.close()
         del psi64, out64
+
+    if a.batched:
+        line["batched"] = batched_line(torch, dev, exx, synth, stream)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(psi_np, r, a.cpu_sample)

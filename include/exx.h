@@ -68,6 +68,9 @@ typedef enum {
 
 /* Plan flags (bitwise or). */
 #define EXX_FLAG_VX_FP64 1u  /* FP32 plans: write vxpsi as double instead of float */
+/* Pair-tile edge T (1..8 orbitals per tile side) chosen by the caller, e.g. from
+ * a tuning run; 0 (no flag) selects the default 8. */
+#define EXX_FLAG_TILE(t) (((unsigned)(t) & 15u) << 8)
 
 /*
  * exx_plan_create -- build a plan for fixed (grid, h, alpha, occupations).

@@ -220,9 +220,9 @@ template <typename T> exx_status_t dalloc(exx_plan_t p, T** out, size_t bytes) {
   return EXX_OK;
 }
 
-int default_tile(int N) {
+int default_tile(int N, int requested) {
   const char* env = std::getenv("EXX_TILE");
-  int T = env ? std::atoi(env) : 8;
+  int T = requested > 0 ? requested : (env ? std::atoi(env) : 8);
   if (T < 1) T = 1;
   if (T > 8) T = 8;
   return T < N ? T : N;
@@ -257,7 +257,9 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
     return EXX_ERR_INVALID_ARG;
   if (precision != EXX_FP64 && precision != EXX_FP32) return EXX_ERR_INVALID_ARG;
   if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY) return EXX_ERR_INVALID_ARG;
-  if (flags & ~(unsigned)EXX_FLAG_VX_FP64) return EXX_ERR_INVALID_ARG;
+  if (flags & ~((unsigned)EXX_FLAG_VX_FP64 | EXX_FLAG_TILE(15))) return EXX_ERR_INVALID_ARG;
+  const int tile_req = (int)((flags >> 8) & 15u);
+  if (tile_req > 8) return EXX_ERR_INVALID_ARG;
   for (int i = 0; i < norb; ++i)
     if (!std::isfinite(occupations[i])) return EXX_ERR_INVALID_ARG;
   if (grid[0] != grid[1] || grid[0] != grid[2] || h[0] != h[1] || h[0] != h[2])
@@ -282,7 +284,7 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
   // pair tiles: blocks of T orbitals, tiles (bi, bj) with bi <= bj
-  p->T = default_tile(norb);
+  p->T = default_tile(norb, tile_req);
   const int T = p->T;
   const int nb = (norb + T - 1) / T;
   std::vector<int4> pairs;

@@ -132,10 +132,11 @@ class ExxPlan:
 
     precision: "fp64" (psi/vxpsi double) or "fp32" (psi float; vxpsi float, or
     double with vx_fp64=True).  kernel: "sinc" (band-limited) or "hockney".
+    tile: pair-tile edge 1..8 (0: the library default; "auto": the tuned value).
     """
 
     def __init__(self, n, h, alpha, occupations, precision="fp32", kernel="sinc",
-                 vx_fp64=False, stream=None):
+                 vx_fp64=False, tile=0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise ExxError(2, "ExxPlan", "no CUDA device: the EXX operator runs only on the GPU")
@@ -154,7 +155,10 @@ class ExxPlan:
         grid = (ctypes.c_int * 3)(self.n, self.n, self.n)
         hh = (ctypes.c_double * 3)(self.h, self.h, self.h)
         handle = ctypes.c_void_p()
-        flags = FLAG_VX_FP64 if self.vx_fp64 else 0
+        if tile == "auto":
+            from . import tune
+            tile = tune.best_tile(self.n, self.norb, precision, tune_if_missing=True)
+        flags = (FLAG_VX_FP64 if self.vx_fp64 else 0) | ((int(tile) & 15) << 8)
         _check(self.lib.exx_plan_create(ctypes.byref(handle), grid, hh, self.alpha,
                                         occ.ctypes.data_as(_c_double_p), self.norb, self.precision,
                                         self.kernel, flags, _stream_ptr(stream)), "exx_plan_create")
@@ -259,7 +263,8 @@ class MolDesc(ctypes.Structure):
 class ExxBatch:
     """Batched FP32 exact exchange over molecules of uneven size.
 
-    mols: list of dicts with keys n, h, alpha, occupations and optional tile.
+    mols: list of dicts with keys n, h, alpha, occupations and optional tile
+    (1..8, 0 for the default, or "auto" for the tuned edge, see tune.py).
     """
 
     def __init__(self, mols, kernel="sinc", stream=None):
@@ -277,7 +282,11 @@ class ExxBatch:
             descs[k].alpha = float(m["alpha"])
             descs[k].occupations = self._occ[k].ctypes.data_as(_c_double_p)
             descs[k].norb = int(self._occ[k].size)
-            descs[k].tile = int(m.get("tile", 0))
+            tile = m.get("tile", 0)
+            if tile == "auto":
+                from . import tune
+                tile = tune.best_tile(descs[k].n, descs[k].norb, "fp32", tune_if_missing=True)
+            descs[k].tile = int(tile)
         handle = ctypes.c_void_p()
         kind = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY}[kernel]
         _check(self.lib.exx_batch_create(ctypes.byref(handle), self.nmol, ctypes.cast(descs, ctypes.c_void_p),

@@ -153,3 +153,26 @@ def test_batched_workload_16_uneven_molecules(env):
             _, eo = o.exx_pair(psi[i], psi[j], Gh, r.h)
             assert abs(Eij[g] - eo) <= 1e-6 * max(1.0, abs(eo)), (k, i, j, Eij[g], eo)
     b.close()
+
+
+def test_tuned_tile_gives_same_results(env, tmp_path, monkeypatch):
+    # the tuner times real applies; any tile edge gives the same result up to
+    # the FP64 accumulation order
+    torch, dev, exx = env
+    from paper_1712_07973_gb300 import tune
+    monkeypatch.setenv("EXX_TUNE_CACHE", str(tmp_path / "tiles.json"))
+    n, N = 16, 10
+    best, timings = tune.tune(n, N, "fp32", reps=2)
+    assert best in timings and len(timings) == 4
+    assert tune.best_tile(n, N, "fp32") == best
+    psi = torch.from_numpy(_mol(n, N, 77, 0.4)).to(dev, torch.float32)
+    occ = np.full(N, 2.0)
+    p0 = exx.ExxPlan(n, 0.4, 0.25, occ, precision="fp32", vx_fp64=True)
+    pa = exx.ExxPlan(n, 0.4, 0.25, occ, precision="fp32", vx_fp64=True, tile="auto")
+    assert pa.info()["tile"] == best
+    E0, v0 = p0.apply(psi)
+    Ea, va = pa.apply(psi)
+    assert abs(Ea - E0) <= 1e-13 * abs(E0)
+    assert torch.allclose(va, v0, rtol=0, atol=1e-12 * float(v0.abs().max()))
+    p0.close()
+    pa.close()
