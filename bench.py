@@ -46,6 +46,9 @@ def args_parse():
     ap.add_argument("--cpu-sample", type=int, default=128, help="pair solves timed on the CPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=["c2_fp32_n96_N64", "c3_grad_n128_N128", "c5_large_n160_N512"],
+                    help="orbital workload of the timed step (default: 64 orbitals on 96^3)")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 16-molecule batched workload (one graph launch)")
     ap.add_argument("--norb", type=int, default=0,
@@ -297,16 +300,21 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     from paper_1712_07973_gb300 import build, exx, synth
     build.build()
-    r, psi_np = synth.workload(WORKLOAD)
-    if a.norb:
-        psi_np = psi_np[: a.norb].copy()
-        r.norb = a.norb
+    big = a.workload != WORKLOAD
+    if big:  # large inputs: generated with the device's help, never copied to the host
+        r, psi = synth.workload(a.workload, dtype=np.float32, device=dev)
+        psi_np = None
+    else:
+        r, psi_np = synth.workload(a.workload)
+        if a.norb:
+            psi_np = psi_np[: a.norb].copy()
+            r.norb = a.norb
+        psi = torch.from_numpy(psi_np).to(dev, torch.float32)
     N, n = r.norb, r.n
     P = N * (N + 1) // 2
     occ = np.full(N, r.occupation)
     plan = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp32")
     info = plan.info()
-    psi = torch.from_numpy(psi_np).to(dev, torch.float32)
     out = torch.empty(psi.shape, dtype=torch.float32, device=dev)
     E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
@@ -360,14 +368,14 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "norb": N, "n": n, "padded": 2 * n, "h": r.h,
+            "config": {"workload": a.workload, "norb": N, "n": n, "padded": 2 * n, "h": r.h,
                        "pairs": P, "tile": info["tile"], "precision": "fp32 ffts, fp64 reductions",
                        "l2": "inputs larger than L2 (psi 226 MB; 0.9 GB pair-tile spectra)",
                        "parallelism": f"replicas x{world}"},
             "E_x": E, "clocks": clocks, "roofline": roofline,
             "gpu_launches": info["launches_apply"] * a.steps}
 
-    golden = os.path.join(ROOT, "tests", "golden", f"{WORKLOAD}.json")
+    golden = os.path.join(ROOT, "tests", "golden", f"{a.workload}.json")
     if a.norb:
         golden = ""
     if os.path.exists(golden):
@@ -376,7 +384,7 @@ def run_ours(a):
 
     # e2e through the host-buffer entry point (pinned memory), every step copies
     # psi in and Vx psi + E_x out
-    psi_h = torch.from_numpy(psi_np.astype(np.float32)).pin_memory()
+    psi_h = (psi.cpu() if big else torch.from_numpy(psi_np.astype(np.float32))).pin_memory()
     vx_h = torch.empty(psi_h.shape, dtype=torch.float32).pin_memory()
     e2e_steps = max(3, min(a.steps, 10))
     plan.apply_host(psi_h, vx_h)
@@ -419,7 +427,7 @@ def run_ours(a):
     del pg
 
     # FP64 plain GPU path on the same workload (the comparison the metric names)
-    if not a.no_fp64:
+    if not a.no_fp64 and not big:
         p64 = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp64")
         psi64 = torch.from_numpy(psi_np).to(dev)
         out64 = torch.empty(psi64.shape, dtype=torch.float64, device=dev)
@@ -442,10 +450,14 @@ def run_ours(a):
         p64.close()
         del psi64, out64
 
-    if a.batched:
+    if a.batched and not big:
         line["batched"] = batched_line(torch, dev, exx, synth, stream)
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        sample = a.cpu_sample if not big else max(4, a.cpu_sample // 16)
+        if big:
+            psi_np = psi.double().cpu().numpy()
+        a.cpu_sample = sample
         rate, dt = cpu_oracle_rate(psi_np, r, a.cpu_sample)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle", "seconds": dt,

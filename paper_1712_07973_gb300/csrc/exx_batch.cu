@@ -20,7 +20,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/exx.h"
+#include "exx.h"
 #include "exx_ops.cuh"
 
 namespace exx_host {

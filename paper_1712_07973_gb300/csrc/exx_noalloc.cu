@@ -21,7 +21,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/exx.h"
+#include "exx.h"
 #include "exx_ops.cuh"
 
 namespace exx_host {

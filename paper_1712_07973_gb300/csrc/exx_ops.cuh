@@ -30,14 +30,17 @@ constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation 
 
 // Launch shape of the slab kernels (fwd_xy, inv_yx): shared memory = fixed
 // part (slab + twiddles) + Q scratch rows.  Two CTAs of 320 threads per SM
-// when at least 8 rows of scratch fit in half an SM, else one CTA of 640.
+// when asked for and at least 8 rows of scratch fit in half an SM, else one
+// CTA of 640 with up to 64 rows.  Measured at n = 96: fwd_xy is faster with
+// two CTAs, inv_yx (whose y pass reads HBM in each batch) with one CTA and
+// fewer, larger batches.
 struct SlabShape {
   int q, nt, minb;
   size_t smem;
 };
-constexpr SlabShape slab_shape(size_t fixed, size_t line) {
+constexpr SlabShape slab_shape(size_t fixed, size_t line, bool prefer_two) {
   const size_t half = 113 * 1024;
-  if (fixed + 8 * line <= half) {
+  if (prefer_two && fixed + 8 * line <= half) {
     size_t q = (half - fixed) / line;
     q = q > 32 ? 32 : q;
     return SlabShape{(int)q, 320, 2, fixed + q * line};
@@ -47,9 +50,11 @@ constexpr SlabShape slab_shape(size_t fixed, size_t line) {
   q = q > 64 ? 64 : q;
   return SlabShape{(int)q, 640, 1, fixed + q * line};
 }
-// zconv warps: a count that divides the L2-long passes when possible
+// zconv warps: a count that divides the L2-long passes when possible (12 for
+// L2 = 12 measured 4% faster than 6 at n = 96)
 constexpr int zconv_warps(int l2) {
-  return (l2 % 8 == 0) ? 8 : (l2 % 6 == 0) ? 6 : (l2 % 7 == 0) ? 7 : (l2 % 5 == 0) ? 5 : 4;
+  return (l2 % 8 == 0) ? 8 : (l2 % 6 == 0) ? 12 : (l2 % 10 == 0) ? 10 : (l2 % 7 == 0) ? 7
+       : (l2 % 5 == 0) ? 5 : 4;
 }
 
 template <typename R, int N> struct OpsImpl {
@@ -60,8 +65,8 @@ template <typename R, int N> struct OpsImpl {
   static constexpr int X1 = split_x(N);
   static constexpr size_t slab = (size_t)(N + 1) * (N + 1) * sizeof(C);
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
-  static constexpr SlabShape SA = slab_shape(slab + (size_t)2 * L * sizeof(C), line);
-  static constexpr SlabShape SC = slab_shape(slab + (size_t)L * sizeof(C), line);
+  static constexpr SlabShape SA = slab_shape(slab + (size_t)2 * L * sizeof(C), line, true);
+  static constexpr SlabShape SC = slab_shape(slab + (size_t)L * sizeof(C), line, false);
   static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb;
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;

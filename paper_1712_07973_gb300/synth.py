@@ -59,8 +59,15 @@ def _sites(rng, r: OrbitalRecipe):
     return rng.uniform(0.2 * L, 0.8 * L, size=(r.nsites, 3))
 
 
-def make_orbitals(r: OrbitalRecipe, dtype=np.float64):
-    """Return psi[norb, n, n, n] (Lowdin-orthonormal, FP64 unless dtype given)."""
+def make_orbitals(r: OrbitalRecipe, dtype=np.float64, device=None):
+    """Return psi[norb, n, n, n] (Lowdin-orthonormal, FP64 unless dtype given).
+
+    With ``device`` (a torch device) the per-orbital contractions and the
+    Lowdin step run there in FP64 and a torch tensor on that device is
+    returned; the random draws are the same NumPy ones.
+    """
+    if device is not None:
+        return _make_orbitals_torch(r, dtype, device)
     rng = np.random.default_rng(r.seed)
     sites = _sites(rng, r)
     x = np.arange(r.n, dtype=np.float64) * r.h
@@ -90,6 +97,37 @@ def make_orbitals(r: OrbitalRecipe, dtype=np.float64):
     return np.ascontiguousarray(psi.astype(dtype, copy=False))
 
 
+def _make_orbitals_torch(r: OrbitalRecipe, dtype, device):
+    import torch
+    rng = np.random.default_rng(r.seed)
+    sites = _sites(rng, r)
+    x = np.arange(r.n, dtype=np.float64) * r.h
+    n, G = r.n, r.gauss_per_orb
+    phi = torch.empty((r.norb, n * n * n), dtype=torch.float64, device=device)
+    for o in range(r.norb):
+        at = rng.integers(0, r.nsites, size=G)
+        sig = rng.uniform(r.sigma[0], r.sigma[1], size=G)
+        coef = rng.standard_normal(G)
+        typ = rng.integers(0, 4, size=G) if r.p_type else np.zeros(G, int)
+        R = sites[at]
+        s2 = 2.0 * sig ** 2
+        dz = x[:, None] - R[None, :, 2]
+        dy = x[:, None] - R[None, :, 1]
+        dx = x[:, None] - R[None, :, 0]
+        gz = np.exp(-dz * dz / s2) * np.where(typ == 3, dz, 1.0) * coef
+        gy = np.exp(-dy * dy / s2) * np.where(typ == 2, dy, 1.0)
+        gx = np.exp(-dx * dx / s2) * np.where(typ == 1, dx, 1.0)
+        gz_t = torch.from_numpy(gz).to(device)
+        yx_t = torch.from_numpy((gy[:, None, :] * gx[None, :, :]).reshape(n * n, G)).to(device)
+        phi[o] = (gz_t @ yx_t.T).reshape(-1)
+    S = (r.h ** 3) * (phi @ phi.T)
+    w, U = torch.linalg.eigh(S)
+    Sm12 = (U / torch.sqrt(w)) @ U.T
+    psi = (Sm12 @ phi).reshape(r.norb, n, n, n)
+    tdt = {np.float64: torch.float64, np.float32: torch.float32}[np.dtype(dtype).type]
+    return psi.to(tdt).contiguous()
+
+
 # Workloads: the five configurations the benchmarks and parity tests use.
 WORKLOADS = {
     # plain FP64: 4 orbitals, 32^3 grid (64^3 padded), 3 s-Gaussians each
@@ -108,9 +146,9 @@ WORKLOADS = {
 }
 
 
-def workload(name, dtype=np.float64):
+def workload(name, dtype=np.float64, device=None):
     r = WORKLOADS[name]
-    return r, make_orbitals(r, dtype=dtype)
+    return r, make_orbitals(r, dtype=dtype, device=device)
 
 
 def batched_workload(seed=3, nmol=16, grids=(48, 64, 80, 96, 112, 128), nrange=(8, 96)):
