@@ -260,6 +260,27 @@ exx_status_t exx_batch_info(exx_batch_t batch, int* ngroups, int* nwaves, size_t
 /* exx_batch_destroy -- free the batch (NULL is a no-op). */
 exx_status_t exx_batch_destroy(exx_batch_t batch);
 
+/*
+ * Sharding over ranks (one GPU per rank).  Pair solves are independent, so a
+ * rank can own a subset of the pair tiles; the only exchange is the sum of
+ * E_x and of Vx psi over ranks (an all-reduce the caller performs, e.g. with
+ * NCCL).  Tiles are assigned largest-first to the least-loaded rank (ties to
+ * the lowest rank), which is deterministic and balances pair solves within one
+ * tile.
+ *
+ * exx_shard_tiles -- host-only: the tile table of a plan with (norb, tile)
+ *   and each tile's owner among nranks.  desc_out: host, 5 ints per tile
+ *   (i0, ti, j0, tj, diag) in the plan's order; owner_out: host, one int per
+ *   tile; either may be NULL to query *ntiles only.  Needs no GPU.
+ * exx_plan_set_shard -- restrict the plan to the tiles of rank `rank` of
+ *   `nranks` (1 rank = everything).  exx_energy / exx_apply then return this
+ *   rank's partial E_x and partial Vx psi; summing them over ranks gives the
+ *   full result.
+ */
+exx_status_t exx_shard_tiles(int norb, int tile, int nranks, int* desc_out, int* owner_out,
+                             int* ntiles);
+exx_status_t exx_plan_set_shard(exx_plan_t plan, int rank, int nranks);
+
 /* exx_plan_destroy -- free the plan and its device memory (NULL is a no-op). */
 exx_status_t exx_plan_destroy(exx_plan_t plan);
 

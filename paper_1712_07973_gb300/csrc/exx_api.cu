@@ -9,6 +9,7 @@
 //   exx_total [-> convert]                                once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -118,6 +119,46 @@ struct Tile {
   int diag;
 };
 
+// Tiles of blocks of T orbitals over the triangle bi <= bj, row-major.
+static std::vector<Tile> make_tiles(int norb, int T) {
+  std::vector<Tile> tiles;
+  const int nb = (norb + T - 1) / T;
+  int off = 0;
+  for (int bi = 0; bi < nb; ++bi)
+    for (int bj = bi; bj < nb; ++bj) {
+      Tile t;
+      t.i0 = bi * T;
+      t.ti = std::min(T, norb - t.i0);
+      t.j0 = bj * T;
+      t.tj = std::min(T, norb - t.j0);
+      t.diag = (bi == bj);
+      t.off = off;
+      t.count = t.diag ? t.ti * (t.ti + 1) / 2 : t.ti * t.tj;
+      off += t.count;
+      tiles.push_back(t);
+    }
+  return tiles;
+}
+
+// Largest-first onto the least-loaded rank (ties: lower tile index first,
+// lowest rank): deterministic, imbalance at most one tile.
+static std::vector<int> shard_owners(const std::vector<Tile>& tiles, int nranks) {
+  std::vector<int> order(tiles.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return tiles[a].count > tiles[b].count; });
+  std::vector<long long> load(nranks, 0);
+  std::vector<int> owner(tiles.size(), 0);
+  for (int k : order) {
+    int r = 0;
+    for (int q = 1; q < nranks; ++q)
+      if (load[q] < load[r]) r = q;
+    owner[k] = r;
+    load[r] += tiles[k].count;
+  }
+  return owner;
+}
+
 }  // namespace exx
 
 using namespace exx;
@@ -130,6 +171,8 @@ struct exx_plan_s {
   const Ops* ops = nullptr;
   int T = 0;
   std::vector<Tile> tiles;
+  std::vector<char> mine;  // tiles this plan processes (all unless sharded)
+  bool sharded = false;
   int maxpairs = 0;
   long long P = 0;
   size_t ws = 0;
@@ -286,26 +329,19 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
   // pair tiles: blocks of T orbitals, tiles (bi, bj) with bi <= bj
   p->T = default_tile(norb, tile_req);
   const int T = p->T;
-  const int nb = (norb + T - 1) / T;
   std::vector<int4> pairs;
-  for (int bi = 0; bi < nb; ++bi)
-    for (int bj = bi; bj < nb; ++bj) {
-      Tile t;
-      t.i0 = bi * T;
-      t.ti = std::min(T, norb - t.i0);
-      t.j0 = bj * T;
-      t.tj = std::min(T, norb - t.j0);
-      t.diag = (bi == bj);
-      t.off = (int)pairs.size();
-      for (int a = 0; a < t.ti; ++a)
-        for (int b = t.diag ? a : 0; b < t.tj; ++b) {
-          const int i = t.i0 + a, j = t.j0 + b;
-          pairs.push_back(make_int4(i, j, (int)tri_start(i, norb) + (j - i), 0));
-        }
-      t.count = (int)pairs.size() - t.off;
-      p->maxpairs = std::max(p->maxpairs, t.count);
-      p->tiles.push_back(t);
-    }
+  for (Tile t : make_tiles(norb, T)) {
+    t.off = (int)pairs.size();
+    for (int a = 0; a < t.ti; ++a)
+      for (int b = t.diag ? a : 0; b < t.tj; ++b) {
+        const int i = t.i0 + a, j = t.j0 + b;
+        pairs.push_back(make_int4(i, j, (int)tri_start(i, norb) + (j - i), 0));
+      }
+    t.count = (int)pairs.size() - t.off;
+    p->maxpairs = std::max(p->maxpairs, t.count);
+    p->tiles.push_back(t);
+  }
+  p->mine.assign(p->tiles.size(), 1);
 
   // kernel spectrum (FP64, host), scaled by the inverse-FFT normalisation
   const size_t m = (size_t)n + 1;
@@ -396,7 +432,8 @@ exx_status_t exx_plan_destroy(exx_plan_t p) {
 exx_status_t exx_plan_info(exx_plan_t p, int* tile, int* ntiles, size_t* workspace_bytes,
                            int* launches_apply, int* launches_energy) {
   if (p == nullptr) return EXX_ERR_INVALID_ARG;
-  const int nt = (int)p->tiles.size();
+  int nt = 0;
+  for (char m : p->mine) nt += m ? 1 : 0;
   if (tile) *tile = p->T;
   if (ntiles) *ntiles = nt;
   if (workspace_bytes) *workspace_bytes = p->ws;
@@ -419,7 +456,11 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
     EXX_CUDA(p, cudaMemsetAsync(acc, 0, (size_t)N * n3 * sizeof(double), st));
   }
   const double c = -p->alpha;
-  for (const Tile& t : p->tiles) {
+  if (p->sharded)  // pair energies of other ranks' tiles must read as zero
+    EXX_CUDA(p, cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st));
+  for (size_t ti = 0; ti < p->tiles.size(); ++ti) {
+    if (!p->mine[ti]) continue;
+    const Tile& t = p->tiles[ti];
     const int4* pr = p->d_pairs + t.off;
     {
       ProfScope ps(p, K_FWD, st);
@@ -565,6 +606,34 @@ exx_status_t exx_profile_read(exx_plan_t p, double* ms, long long* launches, int
       p->cnt[k] = 0;
     }
   }
+  return EXX_OK;
+}
+
+exx_status_t exx_shard_tiles(int norb, int tile, int nranks, int* desc_out, int* owner_out,
+                             int* ntiles) {
+  if (norb < 1 || nranks < 1 || tile < 0 || tile > 8 || ntiles == nullptr) return EXX_ERR_INVALID_ARG;
+  const std::vector<Tile> tiles = make_tiles(norb, default_tile(norb, tile));
+  *ntiles = (int)tiles.size();
+  if (desc_out)
+    for (size_t k = 0; k < tiles.size(); ++k) {
+      desc_out[5 * k + 0] = tiles[k].i0;
+      desc_out[5 * k + 1] = tiles[k].ti;
+      desc_out[5 * k + 2] = tiles[k].j0;
+      desc_out[5 * k + 3] = tiles[k].tj;
+      desc_out[5 * k + 4] = tiles[k].diag;
+    }
+  if (owner_out) {
+    const std::vector<int> own = shard_owners(tiles, nranks);
+    for (size_t k = 0; k < own.size(); ++k) owner_out[k] = own[k];
+  }
+  return EXX_OK;
+}
+
+exx_status_t exx_plan_set_shard(exx_plan_t p, int rank, int nranks) {
+  if (p == nullptr || nranks < 1 || rank < 0 || rank >= nranks) return EXX_ERR_INVALID_ARG;
+  const std::vector<int> own = shard_owners(p->tiles, nranks);
+  for (size_t k = 0; k < own.size(); ++k) p->mine[k] = (own[k] == rank);
+  p->sharded = nranks > 1;
   return EXX_OK;
 }
 

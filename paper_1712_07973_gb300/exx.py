@@ -13,7 +13,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["ExxError", "ExxPlan", "ExxBatch", "load_library", "kernel_spectrum", "EXPORTS",
+__all__ = ["ExxError", "ExxPlan", "ExxBatch", "load_library", "kernel_spectrum", "shard_tiles", "EXPORTS",
            "FP64", "FP32", "KERNEL_SINC", "KERNEL_HOCKNEY", "FLAG_VX_FP64"]
 
 FP64, FP32 = 0, 1
@@ -63,6 +63,9 @@ EXPORTS = {
     "exx_batch_info": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, _c_size_p, _c_int_p,
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "exx_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "exx_shard_tiles": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_int_p, _c_int_p,
+                                       _c_int_p]),
+    "exx_plan_set_shard": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "exx_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "exx_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "exx_version": (ctypes.c_char_p, []),
@@ -110,6 +113,19 @@ def kernel_spectrum(n, h, kind=KERNEL_SINC):
     _check(load_library().exx_kernel_spectrum(n, float(h), int(kind),
                                               out.ctypes.data_as(_c_double_p)), "exx_kernel_spectrum")
     return out.reshape(n + 1, n + 1, n + 1)
+
+
+def shard_tiles(norb, tile=0, nranks=1):
+    """Host-only: tile table (ntiles, 5: i0, ti, j0, tj, diag) and owner ranks."""
+    lib = load_library()
+    nt = ctypes.c_int()
+    _check(lib.exx_shard_tiles(int(norb), int(tile), int(nranks), None, None, ctypes.byref(nt)),
+           "exx_shard_tiles")
+    desc = np.zeros(5 * nt.value, dtype=np.int32)
+    own = np.zeros(nt.value, dtype=np.int32)
+    _check(lib.exx_shard_tiles(int(norb), int(tile), int(nranks), desc.ctypes.data_as(_c_int_p),
+                               own.ctypes.data_as(_c_int_p), ctypes.byref(nt)), "exx_shard_tiles")
+    return desc.reshape(-1, 5), own
 
 
 def _host_ptr(a):
@@ -232,6 +248,10 @@ class ExxPlan:
         _check(self.lib.exx_profile_read(self.handle, ms, cnt, int(bool(reset))),
                "exx_profile_read", self.handle)
         return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KINDS)}
+
+    def set_shard(self, rank, nranks):
+        """Process only this rank's pair tiles (partial E_x and Vx psi)."""
+        _check(self.lib.exx_plan_set_shard(self.handle, int(rank), int(nranks)), "exx_plan_set_shard")
 
     def info(self):
         t, nt, la, le = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -228,3 +228,29 @@ def test_misaligned_caller_pointers(torch_dev):
     assert E1 == E0
     assert torch.allclose(v1, v0, rtol=0, atol=1e-6 * float(v0.abs().max()))
     plan.close()
+
+
+def test_sharded_plans_sum_to_the_whole(torch_dev):
+    # ranks run one after the other on one GPU: their partial E_x and Vx psi
+    # (FP64 outputs) sum to the unsharded result
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    psi = torch.from_numpy(_orbitals(16, 13, seed=61)).to(dev, torch.float32)
+    occ = np.linspace(0.5, 2.0, 13)
+    full = exx.ExxPlan(16, 0.45, 0.25, occ, precision="fp32", vx_fp64=True, tile=4)
+    E0, v0 = full.apply(psi)
+    for R in (2, 3):
+        Es, vs = 0.0, torch.zeros_like(v0)
+        ntiles = 0
+        for rank in range(R):
+            p = exx.ExxPlan(16, 0.45, 0.25, occ, precision="fp32", vx_fp64=True, tile=4)
+            p.set_shard(rank, R)
+            ntiles += p.info()["ntiles"]
+            E, v = p.apply(psi)
+            Es += E
+            vs += v
+            p.close()
+        assert ntiles == full.info()["ntiles"]
+        assert abs(Es - E0) <= 1e-13 * abs(E0)
+        assert torch.allclose(vs, v0, rtol=0, atol=1e-13 * float(v0.abs().max()))
+    full.close()
