@@ -63,7 +63,11 @@ typedef enum {
 typedef enum {
   EXX_KERNEL_SINC = 0,    /* band-limited free-space kernel (default): exact for
                              densities band-limited to the grid's Brillouin zone */
-  EXX_KERNEL_HOCKNEY = 1  /* point-sampled h^3/|r|, cell-averaged origin; O(h^2)  */
+  EXX_KERNEL_HOCKNEY = 1, /* point-sampled h^3/|r|, cell-averaged origin; O(h^2)  */
+  EXX_KERNEL_ERFC = 2     /* band-limited short-range kernel erfc(omega r)/r of
+                             screened hybrids (HSE-type; Sec. 3 notes that only
+                             the Poisson filter changes); needs omega > 0 and
+                             exx_plan_create_desc                                 */
 } exx_kernel_t;
 
 /* Plan flags (bitwise or). */
@@ -92,6 +96,23 @@ typedef enum {
 exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[3],
                              double alpha, const double* occupations, int norb,
                              int precision, int kernel, unsigned flags, void* cuda_stream);
+
+/*
+ * exx_plan_create_desc -- exx_plan_create with every option in one struct,
+ * including the screening parameter omega (bohr^-1) of EXX_KERNEL_ERFC.
+ */
+typedef struct {
+  int grid[3];
+  double h[3];
+  double alpha;
+  const double* occupations;  /* host, norb values; copied */
+  int norb;
+  int precision;              /* exx_precision_t */
+  int kernel;                 /* exx_kernel_t */
+  unsigned flags;             /* EXX_FLAG_* */
+  double omega;               /* EXX_KERNEL_ERFC only: erfc(omega r)/r, omega > 0 */
+} exx_plan_desc;
+exx_status_t exx_plan_create_desc(exx_plan_t* out, const exx_plan_desc* desc, void* cuda_stream);
 
 /*
  * exx_energy -- E_x only (forward transforms and the Parseval sum; no inverse).
@@ -287,10 +308,11 @@ exx_status_t exx_plan_destroy(exx_plan_t plan);
 /*
  * exx_kernel_spectrum -- host-only: the FP64 spectrum of the zero-padded mesh
  * kernel, Ghat[k] = sum_d G~[d] exp(-i pi k.d / n) for k in [0, n]^3 (one
- * octant; Ghat is real and even per axis), unscaled.  out_host holds (n+1)^3
- * doubles, index (kz*(n+1) + ky)*(n+1) + kx.  Needs no GPU.
+ * octant; Ghat is real and even per axis), unscaled.  omega is used by
+ * EXX_KERNEL_ERFC only.  out_host holds (n+1)^3 doubles, index
+ * (kz*(n+1) + ky)*(n+1) + kx.  Needs no GPU.
  */
-exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double* out_host);
+exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double omega, double* out_host);
 
 /* exx_status_string -- static text for a status code. */
 const char* exx_status_string(exx_status_t status);

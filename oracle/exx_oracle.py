@@ -51,6 +51,7 @@ from scipy import integrate as sint
 __all__ = [
     "KERNEL_SINC",
     "KERNEL_HOCKNEY",
+    "KERNEL_ERFC",
     "sinc_kernel_g1d",
     "kernel_real_space",
     "kernel_spectrum",
@@ -64,6 +65,7 @@ __all__ = [
 
 KERNEL_SINC = "sinc"
 KERNEL_HOCKNEY = "hockney"
+KERNEL_ERFC = "erfc"  # band-limited short-range kernel erfc(omega r)/r (screened hybrids)
 
 # --------------------------------------------------------------------------
 # Free-boundary Green's function on the mesh (Sec. 2.1.2; reading above)
@@ -101,7 +103,10 @@ def sinc_kernel_g1d(t, m):
 
 def _sinc_kernel_octant(n):
     """G_BL(m; h=1) for m in [0, n]^3 (octant; G is even per axis)."""
-    s = np.arange(_S_MIN, _S_MAX + 0.5 * _S_STEP, _S_STEP)
+    # nodes at exact multiples of the step (a float-step arange drifts by a few
+    # ulp per node, which biases the rule at the 1e-13 level)
+    K = int(round((_S_MAX - _S_MIN) / _S_STEP))
+    s = _S_MIN + _S_STEP * np.arange(K + 1, dtype=np.float64)
     t = np.exp(s)
     w = _S_STEP * t * (2.0 / math.sqrt(math.pi))
     w[0] *= 0.5
@@ -119,6 +124,24 @@ def _sinc_kernel_octant(n):
     return G
 
 
+def _longrange_octant(n, a):
+    """(2/sqrt(pi)) int_0^a prod_d g(t, m_d) dt for m in [0, n]^3, h = 1.
+
+    The band-limited long-range part erf-like kernel; composite Gauss-Legendre
+    in t on [0, a] (the integrand is analytic there), 64 panels of 16 nodes.
+    """
+    x, w = np.polynomial.legendre.leggauss(16)
+    panels = 64
+    edges = np.linspace(0.0, a, panels + 1)
+    t = (0.5 * (edges[:-1] + edges[1:])[:, None] + 0.5 * np.diff(edges)[:, None] * x[None, :]).ravel()
+    wt = (0.5 * np.diff(edges)[:, None] * w[None, :]).ravel() * (2.0 / math.sqrt(math.pi))
+    m = np.arange(n + 1)
+    g = sinc_kernel_g1d(t, m)
+    gw = g * wt[:, None]
+    ab = (gw[:, :, None] * g[:, None, :]).reshape(t.size, -1)
+    return (ab.T @ g).reshape(n + 1, n + 1, n + 1)
+
+
 def _hockney_cell_average():
     """Average of 1/r over the unit cube centred at the origin.
 
@@ -130,14 +153,22 @@ def _hockney_cell_average():
     return 3.0 * val
 
 
-def kernel_real_space(n, h, kind=KERNEL_SINC):
+def kernel_real_space(n, h, kind=KERNEL_SINC, omega=0.0):
     """Real-space mesh kernel G[m] for m in [0, n]^3, including the h^3 weight.
 
     V[m] = sum_{m'} G[|m - m'|] rho[m'] (absolute difference per axis) is the
-    discrete free-boundary potential of the co-density rho.
+    discrete free-boundary potential of the co-density rho.  KERNEL_ERFC is the
+    band-limited erfc(omega r)/r: the t-integral of the sinc kernel restricted
+    to t > omega (erfc(w r)/r = (2/sqrt pi) int_w^inf exp(-t^2 r^2) dt), i.e.
+    the full kernel minus its t < omega part; in h = 1 units omega becomes
+    omega h.
     """
     if kind == KERNEL_SINC:
         return (h * h) * _sinc_kernel_octant(n)
+    if kind == KERNEL_ERFC:
+        if not omega > 0.0:
+            raise ValueError("the erfc kernel needs omega > 0")
+        return (h * h) * (_sinc_kernel_octant(n) - _longrange_octant(n, omega * h))
     if kind == KERNEL_HOCKNEY:
         m = np.arange(n + 1, dtype=np.float64)
         r = np.sqrt(m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2)

@@ -7,7 +7,7 @@ imported lazily so that the input generator (:mod:`.synth`) can be used
 without loading the CUDA library.
 """
 
-__all__ = ["exx", "autograd", "synth"]
+__all__ = ["exx", "autograd", "synth", "spin", "dist", "tune"]
 
 
 def __getattr__(name):

@@ -21,7 +21,7 @@
 #include "exx_ops.cuh"
 
 namespace exx_host {
-bool kernel_spectrum_octant(int n, double h, int kind, double* out);
+bool kernel_spectrum_octant(int n, double h, int kind, double omega, double* out);
 }
 
 namespace exx {
@@ -166,7 +166,7 @@ using namespace exx;
 struct exx_plan_s {
   int n = 0, N = 0, prec = 0, kind = 0;
   unsigned flags = 0;
-  double h = 0.0, alpha = 0.0;
+  double h = 0.0, alpha = 0.0, omega = 0.0;
   std::vector<double> occ;
   const Ops* ops = nullptr;
   int T = 0;
@@ -283,15 +283,42 @@ const char* exx_last_error(exx_plan_t p) { return p ? p->err.c_str() : ""; }
 
 const char* exx_version(void) { return "exx-gb300 0.1 (sm_103a)"; }
 
-exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double* out_host) {
+exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double omega, double* out_host) {
   if (n < 1 || !(h > 0.0) || out_host == nullptr) return EXX_ERR_INVALID_ARG;
-  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY) return EXX_ERR_INVALID_ARG;
-  return exx_host::kernel_spectrum_octant(n, h, kernel, out_host) ? EXX_OK : EXX_ERR_INVALID_ARG;
+  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC)
+    return EXX_ERR_INVALID_ARG;
+  return exx_host::kernel_spectrum_octant(n, h, kernel, omega, out_host) ? EXX_OK
+                                                                          : EXX_ERR_INVALID_ARG;
 }
+
+static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const double h[3],
+                                     double alpha, const double* occupations, int norb,
+                                     int precision, int kernel, unsigned flags, double omega,
+                                     void* cuda_stream);
 
 exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[3], double alpha,
                              const double* occupations, int norb, int precision, int kernel,
                              unsigned flags, void* cuda_stream) {
+  if (kernel == EXX_KERNEL_ERFC) return EXX_ERR_INVALID_ARG;  // needs omega: exx_plan_create_desc
+  return plan_create_impl(out, grid, h, alpha, occupations, norb, precision, kernel, flags, 0.0,
+                          cuda_stream);
+}
+
+exx_status_t exx_plan_create_desc(exx_plan_t* out, const exx_plan_desc* d, void* cuda_stream) {
+  if (out == nullptr) return EXX_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d == nullptr) return EXX_ERR_INVALID_ARG;
+  if (d->kernel == EXX_KERNEL_ERFC && !(d->omega > 0.0 && std::isfinite(d->omega)))
+    return EXX_ERR_INVALID_ARG;
+  return plan_create_impl(out, d->grid, d->h, d->alpha, d->occupations, d->norb, d->precision,
+                          d->kernel, d->flags, d->kernel == EXX_KERNEL_ERFC ? d->omega : 0.0,
+                          cuda_stream);
+}
+
+static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const double h[3],
+                                     double alpha, const double* occupations, int norb,
+                                     int precision, int kernel, unsigned flags, double omega,
+                                     void* cuda_stream) {
   if (out == nullptr) return EXX_ERR_INVALID_ARG;
   *out = nullptr;
   if (grid == nullptr || h == nullptr || occupations == nullptr) return EXX_ERR_INVALID_ARG;
@@ -299,7 +326,8 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
   if (!(h[0] > 0.0) || !(h[1] > 0.0) || !(h[2] > 0.0) || !std::isfinite(alpha))
     return EXX_ERR_INVALID_ARG;
   if (precision != EXX_FP64 && precision != EXX_FP32) return EXX_ERR_INVALID_ARG;
-  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY) return EXX_ERR_INVALID_ARG;
+  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC)
+    return EXX_ERR_INVALID_ARG;
   if (flags & ~((unsigned)EXX_FLAG_VX_FP64 | EXX_FLAG_TILE(15))) return EXX_ERR_INVALID_ARG;
   const int tile_req = (int)((flags >> 8) & 15u);
   if (tile_req > 8) return EXX_ERR_INVALID_ARG;
@@ -320,6 +348,7 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
   p->flags = flags;
   p->h = h[0];
   p->alpha = alpha;
+  p->omega = omega;
   p->occ.assign(occupations, occupations + norb);
   p->ops = ops;
   p->P = (long long)norb * (norb + 1) / 2;
@@ -346,7 +375,7 @@ exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[
   // kernel spectrum (FP64, host), scaled by the inverse-FFT normalisation
   const size_t m = (size_t)n + 1;
   std::vector<double> Gh(m * m * m);
-  if (!exx_host::kernel_spectrum_octant(n, p->h, kernel, Gh.data())) {
+  if (!exx_host::kernel_spectrum_octant(n, p->h, kernel, p->omega, Gh.data())) {
     delete p;
     return EXX_ERR_INVALID_ARG;
   }

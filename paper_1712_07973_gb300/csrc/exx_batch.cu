@@ -24,7 +24,7 @@
 #include "exx_ops.cuh"
 
 namespace exx_host {
-bool kernel_spectrum_octant(int n, double h, int kind, double* out);
+bool kernel_spectrum_octant(int n, double h, int kind, double omega, double* out);
 }
 
 namespace exx {
@@ -414,7 +414,7 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
   for (Group& g : b->groups) {
     const size_t m = (size_t)g.n + 1;
     std::vector<double> Gh(m * m * m);
-    if (!exx_host::kernel_spectrum_octant(g.n, g.h, kernel, Gh.data())) {
+    if (!exx_host::kernel_spectrum_octant(g.n, g.h, kernel, 0.0, Gh.data())) {
       batch_free(b);
       delete b;
       return EXX_ERR_INVALID_ARG;

@@ -25,7 +25,7 @@
 #include "exx_ops.cuh"
 
 namespace exx_host {
-bool kernel_spectrum_octant(int n, double h, int kind, double* out);
+bool kernel_spectrum_octant(int n, double h, int kind, double omega, double* out);
 }
 namespace exx {
 const Ops* find_ops(int prec, int n);
@@ -100,7 +100,7 @@ exx_status_t load_tables(DeviceScratch& d, const exx::Ops* ops, int n, double h,
                          cudaStream_t st) {
   const size_t m = (size_t)n + 1;
   std::vector<double> G(m * m * m);
-  if (!exx_host::kernel_spectrum_octant(n, h, kind, G.data())) return EXX_ERR_INVALID_ARG;
+  if (!exx_host::kernel_spectrum_octant(n, h, kind, 0.0, G.data())) return EXX_ERR_INVALID_ARG;
   const double L = 2.0 * n;
   const double scale = 1.0 / (L * L * L);
   std::vector<float> Gf(G.size());

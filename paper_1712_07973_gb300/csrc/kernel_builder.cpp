@@ -8,7 +8,9 @@
 //   G[m] = h^3 G_BL(m h),  G_BL(r) = (2 pi)^-3 int_{|k_d| <= pi/h} 4 pi/k^2 e^{ik.r} d^3k,
 //
 // (the exact potential of densities band-limited to the mesh's Brillouin zone)
-// or, on request, the point-sampled Hockney kernel h^3/|m h|.
+// or, on request, the point-sampled Hockney kernel h^3/|m h|, or the
+// band-limited short-range kernel erfc(omega r)/r of screened hybrids, whose
+// t-integral below runs from omega (erfc(w r)/r = (2/sqrt pi) int_w^inf e^{-t^2 r^2} dt).
 //
 // Route used here (distinct from the FP64 oracle's real-space route): with
 // 1/r = (2/sqrt pi) int_0^inf exp(-t^2 r^2) dt every term of the t-integral is
@@ -18,7 +20,7 @@
 //   gh(t,k) = sum_{d=-(n-1)}^{n} g(t,d) cos(pi k d / n)          (windowed DFT)
 //   g(t,x)  = 1/(sqrt(pi) t) int_0^pi exp(-q^2/(4t^2)) cos(q x) dq (h = 1 units)
 //
-// The t-integral uses the exp-sinh rule t = exp(pi/2 sinh s) (double
+// The t-integral uses the exp-sinh rule t = t0 + exp(pi/2 sinh s) (double
 // exponential decay at both ends); g uses composite 16-point Gauss-Legendre in
 // q, or exp(-t^2 x^2) when t <= 0.2 (the neglected tail is below erfc(2.5 pi)).
 // The slot d = n of the periodic embedding is never reached by outputs in
@@ -63,8 +65,9 @@ void gauss_legendre(int m, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
-// Separable (t-node) spectrum: A[t][k] = sqrt-weighted gh(t,k); returns nt.
-void sinc_factors(int n, std::vector<double>& A, std::vector<double>& wt) {
+// Separable (t-node) spectrum: A[t][k] = gh(t,k) at the nodes of the t rule
+// on [t0, inf) (t0 = 0: full Coulomb kernel; t0 = omega h: erfc(omega r)/r).
+void sinc_factors(int n, double t0, std::vector<double>& A, std::vector<double>& wt) {
   // composite Gauss-Legendre on q in [0, pi]: one panel per cosine period of
   // the largest distance, plus margin
   const int gl = 16;
@@ -93,13 +96,13 @@ void sinc_factors(int n, std::vector<double>& A, std::vector<double>& wt) {
       ck[(size_t)k * (n + 1) + d] = c * std::cos(kPi * (double)r / n);
     }
   // exp-sinh nodes
-  const double step = 1.0 / 32.0;
+  const double step = 1.0 / 64.0;
   const double smin = -4.5, smax = 3.6;
   std::vector<double> ts, ws;
   for (double s = smin; s <= smax + 1e-12; s += step) {
-    double t = std::exp(0.5 * kPi * std::sinh(s));
-    double dtds = 0.5 * kPi * std::cosh(s) * t;
-    ts.push_back(t);
+    const double e = std::exp(0.5 * kPi * std::sinh(s));
+    const double dtds = 0.5 * kPi * std::cosh(s) * e;
+    ts.push_back(t0 + e);
     ws.push_back(step * dtds);
   }
   const int nt = (int)ts.size();
@@ -128,9 +131,9 @@ void sinc_factors(int n, std::vector<double>& A, std::vector<double>& wt) {
   }
 }
 
-void sinc_spectrum(int n, double h, double* out) {
+void sinc_spectrum(int n, double h, double a, double* out) {
   std::vector<double> A, wt;
-  sinc_factors(n, A, wt);
+  sinc_factors(n, a, A, wt);
   const int nt = (int)wt.size();
   const int m = n + 1;
   const double pre = h * h * 2.0 / std::sqrt(kPi);
@@ -202,11 +205,13 @@ void hockney_spectrum(int n, double h, double* out) {
 
 }  // namespace
 
-// kind: 0 = band-limited (sinc), 1 = Hockney.  out: (n+1)^3 doubles.
-bool kernel_spectrum_octant(int n, double h, int kind, double* out) {
+// kind: 0 = band-limited (sinc), 1 = Hockney, 2 = band-limited erfc(omega r)/r
+// (omega > 0).  out: (n+1)^3 doubles.
+bool kernel_spectrum_octant(int n, double h, int kind, double omega, double* out) {
   if (n < 1 || !(h > 0.0) || out == nullptr) return false;
-  if (kind == 0) sinc_spectrum(n, h, out);
+  if (kind == 0) sinc_spectrum(n, h, 0.0, out);
   else if (kind == 1) hockney_spectrum(n, h, out);
+  else if (kind == 2 && omega > 0.0 && std::isfinite(omega)) sinc_spectrum(n, h, omega * h, out);
   else return false;
   return true;
 }

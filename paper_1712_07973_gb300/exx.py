@@ -17,7 +17,7 @@ __all__ = ["ExxError", "ExxPlan", "ExxBatch", "load_library", "kernel_spectrum",
            "FP64", "FP32", "KERNEL_SINC", "KERNEL_HOCKNEY", "FLAG_VX_FP64"]
 
 FP64, FP32 = 0, 1
-KERNEL_SINC, KERNEL_HOCKNEY = 0, 1
+KERNEL_SINC, KERNEL_HOCKNEY, KERNEL_ERFC = 0, 1, 2
 FLAG_VX_FP64 = 1
 STATUS = ["EXX_OK", "EXX_ERR_INVALID_ARG", "EXX_ERR_CUDA", "EXX_ERR_OOM", "EXX_ERR_TIMEOUT",
           "EXX_ERR_NOT_SUPPORTED"]
@@ -47,7 +47,10 @@ EXPORTS = {
     "exx_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "exx_profile_read": (ctypes.c_int, [ctypes.c_void_p, _c_double_p,
                                         ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
-    "exx_kernel_spectrum": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, _c_double_p]),
+    "exx_kernel_spectrum": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                           _c_double_p]),
+    "exx_plan_create_desc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                            ctypes.c_void_p]),
     "exx_pair_energy_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                                ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
@@ -107,10 +110,10 @@ def _check(status, where, plan=None):
         raise ExxError(status, where, detail)
 
 
-def kernel_spectrum(n, h, kind=KERNEL_SINC):
+def kernel_spectrum(n, h, kind=KERNEL_SINC, omega=0.0):
     """Host-only FP64 octant of the padded kernel spectrum, shape (n+1,)*3."""
     out = np.zeros((n + 1) ** 3, dtype=np.float64)
-    _check(load_library().exx_kernel_spectrum(n, float(h), int(kind),
+    _check(load_library().exx_kernel_spectrum(n, float(h), int(kind), float(omega),
                                               out.ctypes.data_as(_c_double_p)), "exx_kernel_spectrum")
     return out.reshape(n + 1, n + 1, n + 1)
 
@@ -143,16 +146,24 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+class PlanDesc(ctypes.Structure):
+    """exx_plan_desc of include/exx.h."""
+    _fields_ = [("grid", ctypes.c_int * 3), ("h", ctypes.c_double * 3), ("alpha", ctypes.c_double),
+                ("occupations", _c_double_p), ("norb", ctypes.c_int), ("precision", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("flags", ctypes.c_uint), ("omega", ctypes.c_double)]
+
+
 class ExxPlan:
     """Plan of the exact-exchange operator for fixed grid, h, alpha and occupations.
 
     precision: "fp64" (psi/vxpsi double) or "fp32" (psi float; vxpsi float, or
-    double with vx_fp64=True).  kernel: "sinc" (band-limited) or "hockney".
+    double with vx_fp64=True).  kernel: "sinc" (band-limited), "hockney", or
+    "erfc" (band-limited erfc(omega r)/r, screened hybrids; needs omega > 0).
     tile: pair-tile edge 1..8 (0: the library default; "auto": the tuned value).
     """
 
     def __init__(self, n, h, alpha, occupations, precision="fp32", kernel="sinc",
-                 vx_fp64=False, tile=0, stream=None):
+                 vx_fp64=False, tile=0, omega=0.0, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise ExxError(2, "ExxPlan", "no CUDA device: the EXX operator runs only on the GPU")
@@ -164,7 +175,8 @@ class ExxPlan:
         self.occ = occ
         self.norb = int(occ.size)
         self.precision = {"fp64": FP64, "fp32": FP32}[precision]
-        self.kernel = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY}[kernel]
+        self.kernel = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY, "erfc": KERNEL_ERFC}[kernel]
+        self.omega = float(omega)
         self.vx_fp64 = bool(vx_fp64)
         self.dtype = torch.float64 if self.precision == FP64 else torch.float32
         self.vx_dtype = torch.float64 if (self.precision == FP64 or self.vx_fp64) else torch.float32
@@ -175,9 +187,18 @@ class ExxPlan:
             from . import tune
             tile = tune.best_tile(self.n, self.norb, precision, tune_if_missing=True)
         flags = (FLAG_VX_FP64 if self.vx_fp64 else 0) | ((int(tile) & 15) << 8)
-        _check(self.lib.exx_plan_create(ctypes.byref(handle), grid, hh, self.alpha,
-                                        occ.ctypes.data_as(_c_double_p), self.norb, self.precision,
-                                        self.kernel, flags, _stream_ptr(stream)), "exx_plan_create")
+        d = PlanDesc()
+        d.grid = grid
+        d.h = hh
+        d.alpha = self.alpha
+        d.occupations = occ.ctypes.data_as(_c_double_p)
+        d.norb = self.norb
+        d.precision = self.precision
+        d.kernel = self.kernel
+        d.flags = flags
+        d.omega = self.omega
+        _check(self.lib.exx_plan_create_desc(ctypes.byref(handle), ctypes.byref(d), _stream_ptr(stream)),
+               "exx_plan_create_desc")
         self.handle = handle
 
     # ---------------------------------------------------------------- checks

@@ -82,7 +82,7 @@ def test_host_kernel_spectrum_matches_oracle(lib, n, h):
     from paper_1712_07973_gb300 import exx
     got = exx.kernel_spectrum(n, h, exx.KERNEL_SINC)
     ref = o.kernel_spectrum(o.kernel_real_space(n, h))[: n + 1, : n + 1, : n + 1]
-    assert np.max(np.abs(got - ref)) <= 5e-14 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("n,h", [(6, 0.5), (20, 0.3)])
@@ -96,7 +96,25 @@ def test_host_hockney_spectrum_matches_oracle(lib, n, h):
 def test_kernel_spectrum_rejects_bad_arguments(lib):
     out = np.zeros(8)
     p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    assert lib.exx_kernel_spectrum(0, 0.4, 0, p) == 1
-    assert lib.exx_kernel_spectrum(1, -1.0, 0, p) == 1
-    assert lib.exx_kernel_spectrum(1, 0.4, 3, p) == 1
-    assert lib.exx_kernel_spectrum(1, 0.4, 0, None) == 1
+    assert lib.exx_kernel_spectrum(0, 0.4, 0, 0.0, p) == 1
+    assert lib.exx_kernel_spectrum(1, -1.0, 0, 0.0, p) == 1
+    assert lib.exx_kernel_spectrum(1, 0.4, 3, 0.0, p) == 1
+    assert lib.exx_kernel_spectrum(1, 0.4, 0, 0.0, None) == 1
+    assert lib.exx_kernel_spectrum(1, 0.4, 2, 0.0, p) == 1   # erfc needs omega > 0
+    assert lib.exx_kernel_spectrum(1, 0.4, 2, -0.1, p) == 1
+
+
+@pytest.mark.parametrize("n,h,w", [(8, 0.4, 0.11), (16, 0.3, 0.6), (32, 0.4, 2.0)])
+def test_host_erfc_spectrum_matches_oracle(lib, n, h, w):
+    from paper_1712_07973_gb300 import exx
+    got = exx.kernel_spectrum(n, h, exx.KERNEL_ERFC, omega=w)
+    ref = o.kernel_spectrum(o.kernel_real_space(n, h, o.KERNEL_ERFC, omega=w))[: n + 1, : n + 1, : n + 1]
+    # the oracle forms the short-range kernel as full minus long-range part, so
+    # its rounding is relative to the full kernel's scale
+    full = o.kernel_spectrum(o.kernel_real_space(n, h))
+    assert np.max(np.abs(got - ref)) <= 5e-14 * np.max(np.abs(full))
+
+
+def test_erfc_plan_needs_omega(lib):
+    # the plain constructor refuses the screened kernel (no omega to pass)
+    assert _create(lib, kernel=2)[0] == 1

@@ -35,11 +35,12 @@ def _orbitals(n, N, seed, h=0.45, p_type=True):
     return synth.make_orbitals(r)
 
 
-def _gpu(torch_dev, psi, occ, alpha, h, precision, kernel="sinc", vx_fp64=False):
+def _gpu(torch_dev, psi, occ, alpha, h, precision, kernel="sinc", vx_fp64=False, omega=0.0):
     torch, dev = torch_dev
     from paper_1712_07973_gb300 import exx
     n = psi.shape[1]
-    plan = exx.ExxPlan(n, h, alpha, occ, precision=precision, kernel=kernel, vx_fp64=vx_fp64)
+    plan = exx.ExxPlan(n, h, alpha, occ, precision=precision, kernel=kernel, vx_fp64=vx_fp64,
+                       omega=omega)
     dt = torch.float64 if precision == "fp64" else torch.float32
     p = torch.from_numpy(psi).to(dev, dt)
     E, vx = plan.apply(p)
@@ -49,9 +50,9 @@ def _gpu(torch_dev, psi, occ, alpha, h, precision, kernel="sinc", vx_fp64=False)
     return E, Ee, vx.double().cpu().numpy(), Eij
 
 
-def _oracle(psi, occ, alpha, h, kernel=o.KERNEL_SINC):
+def _oracle(psi, occ, alpha, h, kernel=o.KERNEL_SINC, omega=0.0):
     n = psi.shape[1]
-    Gh = o.kernel_spectrum(o.kernel_real_space(n, h, kernel))
+    Gh = o.kernel_spectrum(o.kernel_real_space(n, h, kernel, omega=omega))
     Ex, vx, Eij = o.exx(psi, occ, alpha, h, Gh)
     return Ex, vx, Eij[np.triu_indices(psi.shape[0])]
 
@@ -254,3 +255,44 @@ def test_sharded_plans_sum_to_the_whole(torch_dev):
         assert abs(Es - E0) <= 1e-13 * abs(E0)
         assert torch.allclose(vs, v0, rtol=0, atol=1e-13 * float(v0.abs().max()))
     full.close()
+
+
+def test_screened_erfc_kernel(torch_dev):
+    # screened hybrids: only the Poisson filter changes (HSE-type erfc(w r)/r)
+    psi = _orbitals(12, 3, seed=33)
+    occ = np.array([2.0, 2.0, 1.0])
+    for w in (0.11, 0.8):
+        _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.45, "fp64", kernel="erfc", omega=w),
+                     _oracle(psi, occ, 0.25, 0.45, o.KERNEL_ERFC, omega=w))
+    # one Gaussian orbital: E_x in closed form with the screened kernel
+    n, h, s = 48, 0.2, 0.6 * math.sqrt(2.0)
+    x = np.arange(n) * h - 0.5 * (n - 1) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    g = ((math.pi * s * s) ** -0.75 * np.exp(-(X * X + Y * Y + Z * Z) / (2 * s * s)))[None]
+    w, sr = 0.6, s / math.sqrt(2.0)
+    E, _, _, _ = _gpu(torch_dev, g, np.array([2.0]), 0.25, h, "fp64", kernel="erfc", omega=w)
+    Eii = math.sqrt(2 / math.pi) * (1 / math.sqrt(2 * sr * sr) - 1 / math.sqrt(2 * sr * sr + 0.5 / (w * w)))
+    assert E == pytest.approx(-0.5 * 0.25 * 4.0 * Eii, rel=1e-10)
+
+
+def test_spin_polarised_channels(torch_dev):
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import spin
+    up = _orbitals(10, 4, seed=81)
+    dn = _orbitals(10, 3, seed=82)
+    fu, fd = np.array([1.0, 1.0, 1.0, 0.5]), np.array([1.0, 1.0, 0.3])
+    sp = spin.ExxSpinPlan(10, 0.45, 0.25, fu, fd, precision="fp64")
+    E, vu, vd = sp.apply(torch.from_numpy(up).to(dev), torch.from_numpy(dn).to(dev))
+    Eu, vxu, _ = _oracle(up, fu, 0.25, 0.45)
+    Ed, vxd, _ = _oracle(dn, fd, 0.25, 0.45)
+    assert abs(E - (Eu + Ed)) <= 1e-10 * abs(Eu + Ed)
+    assert np.max(np.abs(vu.cpu().numpy() - vxu)) <= 1e-10 * np.max(np.abs(vxu))
+    assert np.max(np.abs(vd.cpu().numpy() - vxd)) <= 1e-10 * np.max(np.abs(vxd))
+    # closed shell as two identical channels with f = 1
+    sp2 = spin.ExxSpinPlan(10, 0.45, 0.25, np.ones(4), np.ones(4), precision="fp64")
+    t = torch.from_numpy(up).to(dev)
+    Es = sp2.energy(t, t)
+    E0, _, _, _ = _gpu(torch_dev, up, np.full(4, 2.0), 0.25, 0.45, "fp64")
+    assert Es == pytest.approx(0.5 * E0, rel=1e-13)
+    sp.close()
+    sp2.close()

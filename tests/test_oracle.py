@@ -30,7 +30,7 @@ def test_sinc_kernel_origin_closed_form():
                              epsabs=1e-14, epsrel=1e-14)
     for h in (1.0, 0.4, 0.37):
         G = o.kernel_real_space(4, h)
-        assert G[0, 0, 0] == pytest.approx(h * h * 12.0 * C / math.pi, rel=2e-13)
+        assert G[0, 0, 0] == pytest.approx(h * h * 12.0 * C / math.pi, rel=2e-14)
 
 
 def test_hockney_kernel_origin_closed_form():
@@ -252,3 +252,52 @@ def test_pair_count_matches_paper_table():
         pl = o.pair_list(N)
         assert len(pl) == N * (N + 1) // 2 and len(set(pl)) == len(pl)
         assert all(i <= j for i, j in pl)
+
+
+# ------------------------------------------------------ screened kernel
+
+def test_erfc_kernel_gaussian_potential_and_energy():
+    # Gaussian charge (variance s^2) in the short-range kernel erfc(w r)/r:
+    # V = [erf(r/(sqrt2 s)) - erf(r/sqrt(2 s^2 + 1/w^2))]/r, because erf(w r)/r is
+    # the potential of a Gaussian of variance 1/(2 w^2) and variances add under
+    # convolution; E = int rho V = sqrt(2/pi) [1/sqrt(2 s^2) - 1/sqrt(2 s^2 + 1/(2 w^2))]
+    n, h, sig = 48, 0.2, 0.6
+    for w in (0.11, 0.6, 2.0):
+        r = _centered_grid(n, h)
+        rho = np.exp(-r * r / (2 * sig * sig)) / (2 * math.pi * sig * sig) ** 1.5
+        G = o.kernel_real_space(n, h, o.KERNEL_ERFC, omega=w)
+        V = o.poisson(rho, o.kernel_spectrum(G))
+        s2 = 2 * sig * sig + 1.0 / (w * w)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            Vex = np.where(r > 0, (special.erf(r / (math.sqrt(2) * sig)) - special.erf(r / math.sqrt(s2)))
+                           / np.where(r > 0, r, 1),
+                           math.sqrt(2 / math.pi) / sig - 2.0 / math.sqrt(math.pi * s2))
+        assert np.max(np.abs(V - Vex)) <= 1e-11 * np.max(np.abs(Vex)), w
+        E = h ** 3 * np.sum(rho * V)
+        Eex = math.sqrt(2 / math.pi) * (1 / math.sqrt(2 * sig * sig) - 1 / math.sqrt(2 * sig * sig + 0.5 / (w * w)))
+        assert E == pytest.approx(Eex, rel=1e-11), w
+
+
+def test_erfc_kernel_small_omega_longrange_part_is_point_erf():
+    # for omega h << 1 the t < omega part of the band-limited kernel is the
+    # plain point value h^3 erf(omega |m| h)/(|m| h) (the band edge is far)
+    n, h, w = 12, 0.4, 0.11
+    Gf = o.kernel_real_space(n, h)
+    Gs = o.kernel_real_space(n, h, o.KERNEL_ERFC, omega=w)
+    m = np.arange(n + 1, dtype=float)
+    R = h * np.sqrt(m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        lr = np.where(R > 0, special.erf(w * R) / np.where(R > 0, R, 1), 2 * w / math.sqrt(math.pi))
+    assert np.max(np.abs((Gf - Gs) - h ** 3 * lr)) <= 1e-13 * np.max(np.abs(Gf))
+
+
+def test_closed_shell_as_two_spin_channels():
+    # Eq. HF with per-spin occupations: identical up and down channels with
+    # f = 1 give half the value of the spinless formula with f = 2 (the
+    # occupations enter quadratically), i.e. twice one channel with f = 1
+    r, psi = _small_case(seed=8, n=8, N=3)
+    Gh = o.kernel_spectrum(o.kernel_real_space(r.n, r.h))
+    E1, vx1, _ = o.exx(psi, np.ones(3), 0.25, r.h, Gh)
+    E2, vx2, _ = o.exx(psi, np.full(3, 2.0), 0.25, r.h, Gh)
+    assert 2 * E1 == pytest.approx(0.5 * E2, rel=1e-14)
+    assert np.allclose(2 * vx1, vx2, rtol=1e-14, atol=0)
