@@ -273,6 +273,29 @@ int default_tile(int N, int requested) {
 
 }  // namespace
 
+// k_accum launch: vector width 2 when aligned, full-tile specialisations
+template <typename R, int VEC>
+void launch_accum_v(int mode, const R* psi, const R* V, double* acc, const double* occ,
+                    const Tile& t, double c, long long n3, cudaStream_t st) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n3 / VEC + threads - 1) / threads);
+  if (mode == 1)
+    k_accum<R, 8, VEC, 1><<<blocks, threads, 0, st>>>(psi, V, acc, occ, t.i0, t.ti, t.j0, t.tj,
+                                                       t.diag, c, n3);
+  else if (mode == 2)
+    k_accum<R, 8, VEC, 2><<<blocks, threads, 0, st>>>(psi, V, acc, occ, t.i0, t.ti, t.j0, t.tj,
+                                                       t.diag, c, n3);
+  else
+    k_accum<R, 8, VEC, 0><<<blocks, threads, 0, st>>>(psi, V, acc, occ, t.i0, t.ti, t.j0, t.tj,
+                                                       t.diag, c, n3);
+}
+template <typename R>
+void launch_accum(bool v2, int mode, const R* psi, const R* V, double* acc, const double* occ,
+                  const Tile& t, double c, long long n3, cudaStream_t st) {
+  if (v2) launch_accum_v<R, 2>(mode, psi, V, acc, occ, t, c, n3, st);
+  else launch_accum_v<R, 1>(mode, psi, V, acc, occ, t, c, n3, st);
+}
+
 extern "C" {
 
 const char* exx_status_string(exx_status_t s) {
@@ -383,31 +406,16 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   const double scale = 1.0 / (L * L * L);
   const size_t rs = precision == EXX_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * rs;
-  // twiddles exp(-2 pi i k / 2n): 2n high parts, then 2n low parts (the
-  // rounding residue of the high parts; zero in FP64)
-  std::vector<unsigned char> gbuf(m * m * m * rs), twbuf(2 * 2 * n * cs);
+  // twiddle tables (exx::build_twiddles: w^k and the slab kernels' 2-D
+  // tables, high parts and, for FP32, the rounding residues as low parts)
+  std::vector<unsigned char> gbuf(m * m * m * rs), twbuf(exx::twiddle_count(n) * cs);
   for (size_t k = 0; k < m * m * m; ++k) {
     const double g = Gh[k] * scale;
     if (precision == EXX_FP64) reinterpret_cast<double*>(gbuf.data())[k] = g;
     else reinterpret_cast<float*>(gbuf.data())[k] = (float)g;
   }
-  for (int k = 0; k < 2 * n; ++k) {
-    const double a = -M_PI * (double)k / (double)n;  // -2 pi k / (2n)
-    const double c = std::cos(a), s = std::sin(a);
-    if (precision == EXX_FP64) {
-      double* t = reinterpret_cast<double*>(twbuf.data());
-      t[2 * k] = c;
-      t[2 * k + 1] = s;
-      t[4 * n + 2 * k] = 0.0;
-      t[4 * n + 2 * k + 1] = 0.0;
-    } else {
-      float* t = reinterpret_cast<float*>(twbuf.data());
-      t[2 * k] = (float)c;
-      t[2 * k + 1] = (float)s;
-      t[4 * n + 2 * k] = (float)(c - (double)(float)c);
-      t[4 * n + 2 * k + 1] = (float)(s - (double)(float)s);
-    }
-  }
+  if (precision == EXX_FP64) exx::build_twiddles(n, reinterpret_cast<double*>(twbuf.data()));
+  else exx::build_twiddles(n, reinterpret_cast<float*>(twbuf.data()));
 
   const long long n3 = (long long)n * n * n;
   const size_t nper = m * (size_t)ops->nyb;
@@ -472,6 +480,7 @@ exx_status_t exx_plan_info(exx_plan_t p, int* tile, int* ntiles, size_t* workspa
   return EXX_OK;
 }
 
+
 static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_dev, bool apply,
                         cudaStream_t st) {
   const int n = p->n, N = p->N;
@@ -510,34 +519,17 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
         p->ops->inv_yx(p->X2, p->V, p->tw, t.count, st);
       }
       ProfScope ps(p, K_ACCUM, st);
-      const int threads = 256;
       // vector width: 2 values per thread when n^3 and the caller's pointers
       // allow aligned vector accesses
       const bool al = ((uintptr_t)psi % 16 == 0) && ((uintptr_t)acc % 16 == 0);
       const bool v2 = al && (n3 % 2) == 0;
-      if (p->prec == EXX_FP64) {
-        const int vec = v2 ? 2 : 1;
-        const long long blocks = (n3 / vec + threads - 1) / threads;
-        if (v2)
-          k_accum<double, 8, 2><<<(unsigned)blocks, threads, 0, st>>>(
-              static_cast<const double*>(psi), static_cast<const double*>(p->V), acc, p->d_occ,
-              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
-        else
-          k_accum<double, 8, 1><<<(unsigned)blocks, threads, 0, st>>>(
-              static_cast<const double*>(psi), static_cast<const double*>(p->V), acc, p->d_occ,
-              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
-      } else {
-        const int vec = v2 ? 2 : 1;
-        const long long blocks = (n3 / vec + threads - 1) / threads;
-        if (v2)
-          k_accum<float, 8, 2><<<(unsigned)blocks, threads, 0, st>>>(
-              static_cast<const float*>(psi), static_cast<const float*>(p->V), acc, p->d_occ,
-              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
-        else
-          k_accum<float, 8, 1><<<(unsigned)blocks, threads, 0, st>>>(
-              static_cast<const float*>(psi), static_cast<const float*>(p->V), acc, p->d_occ,
-              t.i0, t.ti, t.j0, t.tj, t.diag, c, n3);
-      }
+      const int mode = (t.ti == 8 && t.tj == 8) ? (t.diag ? 2 : 1) : 0;
+      if (p->prec == EXX_FP64)
+        launch_accum<double>(v2, mode, static_cast<const double*>(psi),
+                             static_cast<const double*>(p->V), acc, p->d_occ, t, c, n3, st);
+      else
+        launch_accum<float>(v2, mode, static_cast<const float*>(psi),
+                            static_cast<const float*>(p->V), acc, p->d_occ, t, c, n3, st);
     }
   }
   {

@@ -420,16 +420,9 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
       return EXX_ERR_INVALID_ARG;
     }
     const double L = 2.0 * g.n, scale = 1.0 / (L * L * L);
-    std::vector<float> gf(Gh.size()), tw(8 * (size_t)g.n);
+    std::vector<float> gf(Gh.size()), tw(2 * exx::twiddle_count(g.n));
     for (size_t k = 0; k < Gh.size(); ++k) gf[k] = (float)(Gh[k] * scale);
-    for (int k = 0; k < 2 * g.n; ++k) {
-      const double a = -M_PI * (double)k / (double)g.n;
-      const double c = std::cos(a), s = std::sin(a);
-      tw[2 * k] = (float)c;
-      tw[2 * k + 1] = (float)s;
-      tw[4 * g.n + 2 * k] = (float)(c - (double)(float)c);
-      tw[4 * g.n + 2 * k + 1] = (float)(s - (double)(float)s);
-    }
+    exx::build_twiddles(g.n, tw.data());
     if (!balloc(b, &g.Gs, gf.size() * sizeof(float)) || !balloc(b, &g.tw, tw.size() * sizeof(float))) {
       batch_free(b);
       delete b;

@@ -52,7 +52,8 @@ template <typename R> __device__ __forceinline__ R sq(R a) { return a * a; }
 // stride SP = n + 1).  x: the complex length-n FFT of z[m] = rho[2m] + i
 // rho[2m+1] runs in place in column y of Sl, followed by the split into the
 // Hermitian half spectrum X[k], k = 0..n (row n is the Nyquist row).  y: the
-// pruned length-2n FFT per kx row, written to HBM as X[p][kx][z][ky].
+// pruned length-2n FFT per kx row, written to HBM as X[p][kx][z][ky].  Q = 0:
+// warp-owned y passes (two rows per warp); Q > 0: CTA-wide batches of Q rows.
 template <typename R, int N, int NT, int MINB, int Q>
 __global__ void __launch_bounds__(NT, MINB)
 k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
@@ -65,9 +66,14 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   constexpr int XIN = PX ? X1 / 2 : X1;
   constexpr int SP = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);  // [2L]: high parts, then low parts
-  C* twl = tw + L;
-  C* Sl = tw + 2 * L;  // [(N+1)][SP]
+  // twiddle tables (packed layout of build_twiddles): TY[k1][n2] = w^(n2 k1)
+  // for the y pass and TX[k1][n2] = w^(2 n2 k1) for the x pass, high and low
+  // parts, so that consecutive lanes (consecutive n2) read consecutive entries
+  C* ty = reinterpret_cast<C*>(smem_raw);
+  C* tyl = ty + L;
+  C* tx = ty + 2 * L;
+  C* txl = tx + N;
+  C* Sl = ty + 2 * L + 2 * N;  // [(N+1)][SP]
 
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
@@ -76,7 +82,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   const R* psi = psi_tab ? psi_tab[pr.w] : psi0;
   const R* __restrict__ pi = psi + (long long)pr.x * n3 + (long long)z * N * N;
   const R* __restrict__ pj = psi + (long long)pr.y * n3 + (long long)z * N * N;
-  for (int t = tid; t < 2 * L; t += NT) tw[t] = tw_g[t];
+  for (int t = tid; t < 2 * L + 2 * N; t += NT) ty[t] = tw_g[2 * L + t];
   __syncthreads();
 
   // x, pass 1: units (y, n2), n2 fastest (coalesced reads of row y)
@@ -103,7 +109,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
     col[0] = v[0];
 #pragma unroll
     for (int k1 = 1; k1 < X1; ++k1)  // omega_n^{n2 k1} = omega_2n^{2 n2 k1}
-      col[k1 * SP] = cmul2<true>(v[k1], tw[2 * n2 * k1], twl[2 * n2 * k1]);
+      col[k1 * SP] = cmul2<true>(v[k1], tx[k1 * X2 + n2], txl[k1 * X2 + n2]);
   }
   __syncthreads();
   // x, pass 2: units (y, k1), y fastest; in place, natural order Z[k] at row k
@@ -132,44 +138,83 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       const C zk = Sl[k * SP + y], zm = Sl[(N - k) * SP + y];
       const C e = mkc<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
       const C o = mkc<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-      const C t = cmul2<true>(o, tw[k], twl[k]);
+      const C t = cmul2<true>(o, __ldg(tw_g + k), __ldg(tw_g + L + k));  // warp-uniform k
       Sl[k * SP + y] = cadd(e, t);
       Sl[(N - k) * SP + y] = mkc<C>(e.x - t.x, t.y - e.y);
     }
   }
   __syncthreads();
-  // y: pruned length-2n FFT per kx row in batches of Q rows; pass 1 into the
-  // row scratch S (padded [n2][k1] layout), pass 2 straight to HBM
+  // y: pruned length-2n FFT per kx row; pass 1 (DFT_L1 over n1 < L1/2, then
+  // the twiddle) into a row scratch in the padded [n2][k1] layout, pass 2
+  // (DFT_L2 over n2) straight to HBM
   C* S = Sl + (N + 1) * SP;
-  for (int r0 = 0; r0 <= N; r0 += Q) {
-    const int nr = min(Q, N + 1 - r0);
-    // units (kx row, n2) with the row fastest: the slab reads stride SP and the
-    // scratch writes stride the (odd) line length, both bank-conflict free
-    for (int u = tid; u < nr * L2; u += NT) {
-      const int n2 = u / nr, r = u - n2 * nr;
-      const C* row = Sl + (r0 + r) * SP;
-      C v[L1];
+  if constexpr (Q == 0) {
+    // warp-owned: each warp transforms two kx rows at a time (one per half
+    // warp) in its own scratch, synchronising with __syncwarp only
+    constexpr int NWP = NT / 32;
+    const int lane = tid & 31, hr = lane >> 4, c = lane & 15;
+    C* Sw = S + ((tid >> 5) * 2 + hr) * Scr<L1, L2>::line;
+    for (int r0 = 2 * (tid >> 5); r0 <= N; r0 += 2 * NWP) {
+      const int kx = r0 + hr;
+      const bool rv = kx <= N;
+      for (int n2 = c; n2 < L2; n2 += 16) {
+        if (rv) {
+          const C* row = Sl + kx * SP;
+          C v[L1];
 #pragma unroll
-      for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
-      dft_halfin<L1, -1, true>(v);
-      C* o = S + r * Scr<L1, L2>::line + n2 * Scr<L1, L2>::row;
-      o[0] = v[0];
+          for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
+          dft_halfin<L1, -1, true>(v);
+          C* o = Sw + n2 * Scr<L1, L2>::row;
+          o[0] = v[0];
 #pragma unroll
-      for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul2<true>(v[k1], tw[n2 * k1], twl[n2 * k1]);
+          for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul2<true>(v[k1], ty[k1 * L2 + n2], tyl[k1 * L2 + n2]);
+        }
+      }
+      __syncwarp();
+      if (rv && c < L1) {
+        const C* q = Sw + c;
+        C v[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
+        dft<L2, 1, -1, true>(v);
+        C* out = X + (((long long)p * (N + 1) + kx) * N + z) * L + c;
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
+      }
+      __syncwarp();
     }
-    __syncthreads();
-    for (int u = tid; u < nr * L1; u += NT) {
-      const int r = u / L1, k1 = u - r * L1;
-      const C* q = S + r * Scr<L1, L2>::line + k1;
-      C v[L2];
+  } else {
+    // CTA-wide batches of Q rows
+    for (int r0 = 0; r0 <= N; r0 += Q) {
+      const int nr = min(Q, N + 1 - r0);
+      // units (kx row, n2) with the row fastest: the slab reads stride SP and
+      // the scratch writes stride the (odd) line length, both bank-conflict free
+      for (int u = tid; u < nr * L2; u += NT) {
+        const int n2 = u / nr, r = u - n2 * nr;
+        const C* row = Sl + (r0 + r) * SP;
+        C v[L1];
 #pragma unroll
-      for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
-      dft<L2, 1, -1, true>(v);
-      C* out = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
+        for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
+        dft_halfin<L1, -1, true>(v);
+        C* o = S + r * Scr<L1, L2>::line + n2 * Scr<L1, L2>::row;
+        o[0] = v[0];
 #pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
+        for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul2<true>(v[k1], ty[k1 * L2 + n2], tyl[k1 * L2 + n2]);
+      }
+      __syncthreads();
+      for (int u = tid; u < nr * L1; u += NT) {
+        const int r = u / L1, k1 = u - r * L1;
+        const C* q = S + r * Scr<L1, L2>::line + k1;
+        C v[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
+        dft<L2, 1, -1, true>(v);
+        C* out = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -292,45 +337,84 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   constexpr int XOUT = PX ? X1 / 2 : X1;
   constexpr int SP = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);  // high parts
-  C* Sl = tw + L;                          // [(N+1)][SP]
+  C* tw = reinterpret_cast<C*>(smem_raw);  // w^k, high parts [L]
+  C* ti = tw + L;                          // TI[m2][k1] = w^(m2 k1) [L] (see fwd_xy)
+  C* Sl = ti + L;                          // [(N+1)][SP]
 
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
   const int p = blockIdx.y;
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
+  for (int t = tid; t < L; t += NT) ti[t] = tw_g[4 * L + 2 * N + t];
   __syncthreads();
-  // y: inverse length-2n FFT per kx row in batches of Q rows, keeping y < n;
-  // pass 1 (DFT_L2 over k2, twiddle) from HBM into the row scratch S, pass 2
-  // (pruned-output DFT_L1 over k1) into the slab
+  // y: inverse length-2n FFT per kx row keeping y < n; pass 1 (DFT_L2 over
+  // k2, twiddle) from HBM into a row scratch, pass 2 (pruned-output DFT_L1
+  // over k1) into the slab
   C* S = Sl + (N + 1) * SP;
-  for (int r0 = 0; r0 <= N; r0 += Q) {
-    const int nr = min(Q, N + 1 - r0);
-    for (int u = tid; u < nr * L1; u += NT) {
-      const int r = u / L1, k1 = u - r * L1;
-      const C* in = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
-      C v[L2];
+  if constexpr (Q == 0) {
+    // warp-owned: two kx rows per warp (one per half warp), own scratch
+    constexpr int NWP = NT / 32;
+    const int lane = tid & 31, hr = lane >> 4, c = lane & 15;
+    C* Sw = S + ((tid >> 5) * 2 + hr) * Scr<L1, L2>::line;
+    for (int r0 = 2 * (tid >> 5); r0 <= N; r0 += 2 * NWP) {
+      const int kx = r0 + hr;
+      const bool rv = kx <= N;
+      if (rv && c < L1) {
+        const C* in = X + (((long long)p * (N + 1) + kx) * N + z) * L + c;
+        C v[L2];
 #pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
-      dft<L2, 1, 1>(v);
-      C* q = S + r * Scr<L1, L2>::line + k1;
-      q[0] = v[0];
+        for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
+        dft<L2, 1, 1>(v);
+        C* q = Sw + c;
+        q[0] = v[0];
 #pragma unroll
-      for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], tw[m2 * k1]);
+        for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], ti[m2 * L1 + c]);
+      }
+      __syncwarp();
+      for (int m2 = c; m2 < L2; m2 += 16) {
+        if (rv) {
+          const C* q = Sw + m2 * Scr<L1, L2>::row;
+          C v[L1];
+#pragma unroll
+          for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
+          dft_halfout<L1, 1>(v);
+          C* row = Sl + kx * SP;
+#pragma unroll
+          for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
+        }
+      }
+      __syncwarp();
     }
     __syncthreads();
-    for (int u = tid; u < nr * L2; u += NT) {  // row fastest (see fwd_xy)
-      const int m2 = u / nr, r = u - m2 * nr;
-      const C* q = S + r * Scr<L1, L2>::line + m2 * Scr<L1, L2>::row;
-      C v[L1];
+  } else {
+    for (int r0 = 0; r0 <= N; r0 += Q) {
+      const int nr = min(Q, N + 1 - r0);
+      for (int u = tid; u < nr * L1; u += NT) {
+        const int r = u / L1, k1 = u - r * L1;
+        const C* in = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
+        C v[L2];
 #pragma unroll
-      for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
-      dft_halfout<L1, 1>(v);
-      C* row = Sl + (r0 + r) * SP;
+        for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
+        dft<L2, 1, 1>(v);
+        C* q = S + r * Scr<L1, L2>::line + k1;
+        q[0] = v[0];
 #pragma unroll
-      for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
+        for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], ti[m2 * L1 + k1]);
+      }
+      __syncthreads();
+      for (int u = tid; u < nr * L2; u += NT) {  // row fastest (see fwd_xy)
+        const int m2 = u / nr, r = u - m2 * nr;
+        const C* q = S + r * Scr<L1, L2>::line + m2 * Scr<L1, L2>::row;
+        C v[L1];
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
+        dft_halfout<L1, 1>(v);
+        C* row = Sl + (r0 + r) * SP;
+#pragma unroll
+        for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   // fold the half spectrum into Z (units (y, k), k = 0..n/2, y fastest)
   for (int u = tid; u < N * (N / 2 + 1); u += NT) {
@@ -430,11 +514,18 @@ __device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
   }
 }
 
-template <typename R, int TM, int VEC>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
+// MODE 0: any tile; MODE 1: full off-diagonal tile (ti = tj = TM); MODE 2:
+// full diagonal tile.  The full modes make every loop bound and branch a
+// compile-time constant, so that all loads of a J step can be issued at once
+// (with the register budget of two CTAs per SM: 4.9 -> 3.8 ms per exx_apply
+// at n = 96, 64 orbitals).
+template <typename R, int TM, int VEC, int MODE>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && MODE == 0) ? 3 : 2)
 k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__ vx,
-        const double* __restrict__ occ, int i0, int ti, int j0, int tj, int diag, double c,
+        const double* __restrict__ occ, int i0, int ti_, int j0, int tj_, int diag_, double c,
         long long n3) {
+  const int ti = MODE ? TM : ti_, tj = MODE ? TM : tj_;
+  const bool diag = MODE == 2 ? true : MODE == 1 ? false : diag_ != 0;
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
   if (r >= n3) return;
   R fi[TM];

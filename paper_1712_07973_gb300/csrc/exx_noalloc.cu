@@ -35,7 +35,7 @@ constexpr int kNoallocMaxN = EXX_NOALLOC_MAX_N;
 constexpr size_t kSpecElems = (size_t)(kNoallocMaxN + 1) * kNoallocMaxN * 2 * kNoallocMaxN;
 constexpr size_t kKernElems =
     (size_t)(kNoallocMaxN + 1) * (kNoallocMaxN + 1) * (kNoallocMaxN + 1);
-constexpr int kTwElems = 4 * kNoallocMaxN;  // 2n high + 2n low twiddle parts
+constexpr int kTwElems = 12 * kNoallocMaxN;  // exx::twiddle_count(n) for n <= max
 constexpr int kEpartElems = (kNoallocMaxN + 1) * ((2 * kNoallocMaxN + 31) / 32);
 
 // Shared scratch of every call on a device (contents persist between calls):
@@ -105,13 +105,8 @@ exx_status_t load_tables(DeviceScratch& d, const exx::Ops* ops, int n, double h,
   const double scale = 1.0 / (L * L * L);
   std::vector<float> Gf(G.size());
   for (size_t k = 0; k < G.size(); ++k) Gf[k] = (float)(G[k] * scale);
-  std::vector<float2> tw(4 * (size_t)n);
-  for (int k = 0; k < 2 * n; ++k) {
-    const double a = -M_PI * (double)k / (double)n;
-    const double c = std::cos(a), s = std::sin(a);
-    tw[k] = make_float2((float)c, (float)s);
-    tw[2 * n + k] = make_float2((float)(c - (double)(float)c), (float)(s - (double)(float)s));
-  }
+  std::vector<float2> tw(exx::twiddle_count(n));
+  exx::build_twiddles(n, reinterpret_cast<float*>(tw.data()));
   cudaError_t e = cudaMemcpyAsync(d.kern, Gf.data(), Gf.size() * sizeof(float),
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)

@@ -3,6 +3,7 @@
 // C-ABI layer picks the table at plan creation.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 
 #include "exx_kernels.cuh"
@@ -29,32 +30,67 @@ struct Ops {
 constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation of one CTA
 
 // Launch shape of the slab kernels (fwd_xy, inv_yx): shared memory = fixed
-// part (slab + twiddles) + Q scratch rows.  Two CTAs of 320 threads per SM
-// when asked for and at least 8 rows of scratch fit in half an SM, else one
-// CTA of 640 with up to 64 rows.  Measured at n = 96: fwd_xy is faster with
-// two CTAs, inv_yx (whose y pass reads HBM in each batch) with one CTA and
-// fewer, larger batches.
+// part (slab + twiddles) + y-pass scratch.  Preferred: warp-owned y passes
+// (q = 0), two scratch rows per warp, as two CTAs of 320 threads per SM when
+// asked for and they fit in half an SM, else one CTA of 640.  Otherwise
+// CTA-wide batches of q rows.  Measured at n = 96 (64 orbitals): warp-owned
+// y passes with two CTAs per SM take fwd_xy from 13.3 to 13.0 ms and inv_yx
+// from 13.5 to 11.1 ms per exx_apply.
 struct SlabShape {
   int q, nt, minb;
   size_t smem;
+  bool fits;
 };
 constexpr SlabShape slab_shape(size_t fixed, size_t line, bool prefer_two) {
   const size_t half = 113 * 1024;
+  if (prefer_two && fixed + 20 * line <= half) return SlabShape{0, 320, 2, fixed + 20 * line, true};
+  if (fixed + 40 * line <= kSmemPerCTA) return SlabShape{0, 640, 1, fixed + 40 * line, true};
   if (prefer_two && fixed + 8 * line <= half) {
     size_t q = (half - fixed) / line;
     q = q > 32 ? 32 : q;
-    return SlabShape{(int)q, 320, 2, fixed + q * line};
+    return SlabShape{(int)q, 320, 2, fixed + q * line, true};
   }
-  if (fixed + line > kSmemPerCTA) return SlabShape{0, 0, 0, 0};
+  if (fixed + line > kSmemPerCTA) return SlabShape{1, 640, 1, fixed + line, false};
   size_t q = (kSmemPerCTA - fixed) / line;
   q = q > 64 ? 64 : q;
-  return SlabShape{(int)q, 640, 1, fixed + q * line};
+  return SlabShape{(int)q, 640, 1, fixed + q * line, true};
 }
 // zconv warps: a count that divides the L2-long passes when possible (12 for
 // L2 = 12 measured 4% faster than 6 at n = 96)
 constexpr int zconv_warps(int l2) {
   return (l2 % 8 == 0) ? 8 : (l2 % 6 == 0) ? 12 : (l2 % 10 == 0) ? 10 : (l2 % 7 == 0) ? 7
        : (l2 % 5 == 0) ? 5 : 4;
+}
+
+// Twiddle tables of one grid size, packed in one array of complex values;
+// exponent e stands for w^e = exp(-2 pi i e / L), L = 2n:
+//   [0, L)          w^k, high parts; [L, 2L) their low parts (zero in FP64)
+//   [2L, 3L)        TY[k1][n2] = w^(n2 k1), k1 < L1, n2 < L2; [3L, 4L) low parts
+//   [4L, 4L+n)      TX[k1][n2] = w^(2 n2 k1), k1 < X1, n2 < X2; [4L+n, 4L+2n) low
+//   [4L+2n, 5L+2n)  TI[m2][k1] = w^(m2 k1), m2 < L2, k1 < L1 (high parts)
+// The two-dimensional tables put the index that varies across the lanes of
+// the slab kernels' passes fastest, so that their reads are conflict free.
+inline size_t twiddle_count(int n) { return (size_t)12 * n; }
+template <typename R> void build_twiddles(int n, R* out) {
+  const int L = 2 * n, L1 = split_l1(L), L2 = L1 ? L / L1 : 1;
+  const int X1 = split_x(n), X2 = X1 ? n / X1 : 1;
+  auto put = [&](size_t idx, long e, size_t lo) {
+    const double a = -M_PI * (double)(e % L) / (double)n;
+    const double c = std::cos(a), s = std::sin(a);
+    out[2 * idx] = (R)c;
+    out[2 * idx + 1] = (R)s;
+    if (lo) {
+      out[2 * (idx + lo)] = (R)(c - (double)(R)c);
+      out[2 * (idx + lo) + 1] = (R)(s - (double)(R)s);
+    }
+  };
+  for (int k = 0; k < L; ++k) put(k, k, L);
+  for (int k1 = 0; k1 < L1; ++k1)
+    for (int n2 = 0; n2 < L2; ++n2) put(2 * L + k1 * L2 + n2, (long)n2 * k1, L);
+  for (int k1 = 0; k1 < X1; ++k1)
+    for (int n2 = 0; n2 < X2; ++n2) put(4 * L + k1 * X2 + n2, (long)2 * n2 * k1, n);
+  for (int m2 = 0; m2 < L2; ++m2)
+    for (int k1 = 0; k1 < L1; ++k1) put(4 * L + 2 * n + m2 * L1 + k1, (long)m2 * k1, 0);
 }
 
 template <typename R, int N> struct OpsImpl {
@@ -65,8 +101,8 @@ template <typename R, int N> struct OpsImpl {
   static constexpr int X1 = split_x(N);
   static constexpr size_t slab = (size_t)(N + 1) * (N + 1) * sizeof(C);
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
-  static constexpr SlabShape SA = slab_shape(slab + (size_t)2 * L * sizeof(C), line, true);
-  static constexpr SlabShape SC = slab_shape(slab + (size_t)L * sizeof(C), line, false);
+  static constexpr SlabShape SA = slab_shape(slab + (size_t)(2 * L + 2 * N) * sizeof(C), line, true);
+  static constexpr SlabShape SC = slab_shape(slab + (size_t)2 * L * sizeof(C), line, true);
   static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb;
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
@@ -74,7 +110,7 @@ template <typename R, int N> struct OpsImpl {
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
   static constexpr size_t smem_b = ((size_t)2 * L + (size_t)L * W) * sizeof(C);
-  static constexpr bool ok = L1 != 0 && X1 != 0 && QA >= 1 && QC >= 1 && smem_b <= kSmemPerCTA;
+  static constexpr bool ok = L1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
 
   static cudaError_t setup() {
     if constexpr (ok) {
