@@ -406,16 +406,23 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   const double scale = 1.0 / (L * L * L);
   const size_t rs = precision == EXX_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * rs;
-  // twiddle tables (exx::build_twiddles: w^k and the slab kernels' 2-D
-  // tables, high parts and, for FP32, the rounding residues as low parts)
-  std::vector<unsigned char> gbuf(m * m * m * rs), twbuf(exx::twiddle_count(n) * cs);
-  for (size_t k = 0; k < m * m * m; ++k) {
-    const double g = Gh[k] * scale;
-    if (precision == EXX_FP64) reinterpret_cast<double*>(gbuf.data())[k] = g;
-    else reinterpret_cast<float*>(gbuf.data())[k] = (float)g;
+  // kernel table (scaled by 1/(2n)^3; for FP32 with the forward transforms'
+  // gains divided out) and twiddle tables (exx_ops.cuh)
+  std::vector<unsigned char> gbuf(exx::kernel_table_bytes(n, rs)), twbuf(exx::twiddle_count(n) * cs);
+  std::vector<double> gx, gz;
+  if (ops->gains) {
+    gx.resize(m);
+    gz.resize(2 * (size_t)n);
+    ops->gains(gx.data(), gz.data());
   }
-  if (precision == EXX_FP64) exx::build_twiddles(n, reinterpret_cast<double*>(twbuf.data()));
-  else exx::build_twiddles(n, reinterpret_cast<float*>(twbuf.data()));
+  if (precision == EXX_FP64) {
+    exx::build_kernel_table<double>(n, Gh.data(), scale, nullptr, nullptr, gbuf.data());
+    exx::build_twiddles(n, reinterpret_cast<double*>(twbuf.data()));
+  } else {
+    exx::build_kernel_table<float>(n, Gh.data(), scale, gx.empty() ? nullptr : gx.data(),
+                                   gz.empty() ? nullptr : gz.data(), gbuf.data());
+    exx::build_twiddles(n, reinterpret_cast<float*>(twbuf.data()));
+  }
 
   const long long n3 = (long long)n * n * n;
   const size_t nper = m * (size_t)ops->nyb;

@@ -410,7 +410,6 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
   if (e == cudaSuccess) e = cudaMemsetAsync(b->Epair, 0, (size_t)ep * sizeof(double), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_vx_tab, 0, nmol * sizeof(float*), st);
   // kernel spectra and twiddles per group
-  std::vector<std::vector<float>> keep;
   for (Group& g : b->groups) {
     const size_t m = (size_t)g.n + 1;
     std::vector<double> Gh(m * m * m);
@@ -420,15 +419,18 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
       return EXX_ERR_INVALID_ARG;
     }
     const double L = 2.0 * g.n, scale = 1.0 / (L * L * L);
-    std::vector<float> gf(Gh.size()), tw(2 * exx::twiddle_count(g.n));
-    for (size_t k = 0; k < Gh.size(); ++k) gf[k] = (float)(Gh[k] * scale);
+    std::vector<double> gx(m), gz(2 * (size_t)g.n);
+    g.ops->gains(gx.data(), gz.data());
+    std::vector<unsigned char> gf(exx::kernel_table_bytes(g.n, sizeof(float)));
+    exx::build_kernel_table<float>(g.n, Gh.data(), scale, gx.data(), gz.data(), gf.data());
+    std::vector<float> tw(2 * exx::twiddle_count(g.n));
     exx::build_twiddles(g.n, tw.data());
-    if (!balloc(b, &g.Gs, gf.size() * sizeof(float)) || !balloc(b, &g.tw, tw.size() * sizeof(float))) {
+    if (!balloc(b, &g.Gs, gf.size()) || !balloc(b, &g.tw, tw.size() * sizeof(float))) {
       batch_free(b);
       delete b;
       return EXX_ERR_OOM;
     }
-    up(g.Gs, gf.data(), gf.size() * sizeof(float));
+    up(g.Gs, gf.data(), gf.size());
     up(g.tw, tw.data(), tw.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host buffers die at scope end
     if (e == cudaSuccess) e = g.ops->setup();

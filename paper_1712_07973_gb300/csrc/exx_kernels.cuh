@@ -47,6 +47,36 @@ template <int L1, int L2> struct Scr {
 
 template <typename R> __device__ __forceinline__ R sq(R a) { return a * a; }
 
+// 16-byte asynchronous global -> shared copy (cp.async); src_bytes = 0 fills
+// the destination with zeros without reading.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Kernel table of zconv (built by build_kernel_table): Gt[kx][kz][ky],
+// kx <= n, kz, ky < 2n, the scaled kernel spectrum divided by the energy
+// gains |dx(kx)|^2 |dy(ky)|^2 |dz(kz)|^2 of the FP32 forward transforms (1 in
+// FP64).  Stored unfolded (Ghat is even in ky and kz) so that the gains,
+// which are not, are divided out in the table itself.
+
+// One step of the split of the complex length-n spectrum Z of the (even, odd)
+// sample pairs into the Hermitian half spectrum X of the real length-2n line:
+// for zk = Z[k], zm = Z[n-k] (0 < k, 2k != n) and w = omega_2n^k,
+// X[k] = E + w O and X[n-k] = conj(E - w O), E = (zk + conj zm) / 2,
+// O = (zk - conj zm) / (2i).
+template <typename C> EXX_HD void split_step(C zk, C zm, C w, C& xk, C& xm) {
+  using R = typename creal<C>::type;
+  const C e = mkc<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
+  const C o = mkc<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
+  const C t = cmul(o, w);
+  xk = cadd(e, t);
+  xm = mkc<C>(e.x - t.x, t.y - e.y);
+}
+
 // ------------------------------------------------------------------ fwd_xy
 // One CTA per (z-slab, pair).  Shared memory holds the slab Sl[k][y] (row
 // stride SP = n + 1).  x: the complex length-n FFT of z[m] = rho[2m] + i
@@ -67,13 +97,11 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   constexpr int SP = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // twiddle tables (packed layout of build_twiddles): TY[k1][n2] = w^(n2 k1)
-  // for the y pass and TX[k1][n2] = w^(2 n2 k1) for the x pass, high and low
-  // parts, so that consecutive lanes (consecutive n2) read consecutive entries
+  // for the y pass and TX[k1][n2] = w^(2 n2 k1) for the x pass, so that
+  // consecutive lanes (consecutive n2) read consecutive entries
   C* ty = reinterpret_cast<C*>(smem_raw);
-  C* tyl = ty + L;
-  C* tx = ty + 2 * L;
-  C* txl = tx + N;
-  C* Sl = ty + 2 * L + 2 * N;  // [(N+1)][SP]
+  C* tx = ty + L;
+  C* Sl = tx + N;  // [(N+1)][SP]
 
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
@@ -82,7 +110,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   const R* psi = psi_tab ? psi_tab[pr.w] : psi0;
   const R* __restrict__ pi = psi + (long long)pr.x * n3 + (long long)z * N * N;
   const R* __restrict__ pj = psi + (long long)pr.y * n3 + (long long)z * N * N;
-  for (int t = tid; t < 2 * L + 2 * N; t += NT) ty[t] = tw_g[2 * L + t];
+  for (int t = tid; t < L + N; t += NT) ty[t] = tw_g[L + t];
   __syncthreads();
 
   // x, pass 1: units (y, n2), n2 fastest (coalesced reads of row y)
@@ -99,17 +127,17 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       v[n1] = mkc<C>(a, b);
     }
     if constexpr (PX) {
-      dft_halfin<X1, -1, true>(v);
+      dft_halfin<X1, -1>(v);
     } else {
 #pragma unroll
       for (int n1 = XIN; n1 < X1; ++n1) v[n1] = mkc<C>(R(0), R(0));
-      dft<X1, 1, -1, true>(v);
+      dft<X1, 1, -1>(v);
     }
     C* col = Sl + (n2 * X1) * SP + y;
     col[0] = v[0];
 #pragma unroll
     for (int k1 = 1; k1 < X1; ++k1)  // omega_n^{n2 k1} = omega_2n^{2 n2 k1}
-      col[k1 * SP] = cmul2<true>(v[k1], tx[k1 * X2 + n2], txl[k1 * X2 + n2]);
+      col[k1 * SP] = cmul(v[k1], tx[k1 * X2 + n2]);
   }
   __syncthreads();
   // x, pass 2: units (y, k1), y fastest; in place, natural order Z[k] at row k
@@ -118,7 +146,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
     C v[X2];
 #pragma unroll
     for (int n2 = 0; n2 < X2; ++n2) v[n2] = Sl[(n2 * X1 + k1) * SP + y];
-    dft<X2, 1, -1, true>(v);
+    dft<X2, 1, -1>(v);
 #pragma unroll
     for (int k2 = 0; k2 < X2; ++k2) Sl[(k1 + X1 * k2) * SP + y] = v[k2];
   }
@@ -135,12 +163,10 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       const C zk = Sl[k * SP + y];
       Sl[k * SP + y] = mkc<C>(zk.x, -zk.y);
     } else {
-      const C zk = Sl[k * SP + y], zm = Sl[(N - k) * SP + y];
-      const C e = mkc<C>(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y - zm.y));
-      const C o = mkc<C>(R(0.5) * (zk.y + zm.y), R(-0.5) * (zk.x - zm.x));
-      const C t = cmul2<true>(o, __ldg(tw_g + k), __ldg(tw_g + L + k));  // warp-uniform k
-      Sl[k * SP + y] = cadd(e, t);
-      Sl[(N - k) * SP + y] = mkc<C>(e.x - t.x, t.y - e.y);
+      C xk, xm;
+      split_step(Sl[k * SP + y], Sl[(N - k) * SP + y], __ldg(tw_g + k), xk, xm);  // uniform k
+      Sl[k * SP + y] = xk;
+      Sl[(N - k) * SP + y] = xm;
     }
   }
   __syncthreads();
@@ -163,11 +189,11 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
           C v[L1];
 #pragma unroll
           for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
-          dft_halfin<L1, -1, true>(v);
+          dft_halfin<L1, -1>(v);
           C* o = Sw + n2 * Scr<L1, L2>::row;
           o[0] = v[0];
 #pragma unroll
-          for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul2<true>(v[k1], ty[k1 * L2 + n2], tyl[k1 * L2 + n2]);
+          for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul(v[k1], ty[k1 * L2 + n2]);
         }
       }
       __syncwarp();
@@ -176,7 +202,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
         C v[L2];
 #pragma unroll
         for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
-        dft<L2, 1, -1, true>(v);
+        dft<L2, 1, -1>(v);
         C* out = X + (((long long)p * (N + 1) + kx) * N + z) * L + c;
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
@@ -195,11 +221,11 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
         C v[L1];
 #pragma unroll
         for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
-        dft_halfin<L1, -1, true>(v);
+        dft_halfin<L1, -1>(v);
         C* o = S + r * Scr<L1, L2>::line + n2 * Scr<L1, L2>::row;
         o[0] = v[0];
 #pragma unroll
-        for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul2<true>(v[k1], ty[k1 * L2 + n2], tyl[k1 * L2 + n2]);
+        for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul(v[k1], ty[k1 * L2 + n2]);
       }
       __syncthreads();
       for (int u = tid; u < nr * L1; u += NT) {
@@ -208,7 +234,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
         C v[L2];
 #pragma unroll
         for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
-        dft<L2, 1, -1, true>(v);
+        dft<L2, 1, -1>(v);
         C* out = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
@@ -219,104 +245,124 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 }
 
 // ------------------------------------------------------------------- zconv
-// One CTA per (32 consecutive ky columns, kx, pair); lane = column, warps
-// share the sub-DFTs of each pass.  Along z: pruned forward FFT (pass 1 of
-// length L1 over z = L2 n1 + n2, pass 2 of length L2), multiply by
-// Ghat/(2n)^3 with the Parseval energy w(kx) Ghat |rho_hat|^2, inverse FFT
-// keeping z < n.  In place on X.
-template <typename R, int N, int NW, bool ENERGY_ONLY>
-__global__ void __launch_bounds__(32 * NW)
+// One CTA per (32 consecutive ky columns, kx, PPC consecutive pairs); lane =
+// column, warps share the sub-DFTs of each pass.  Along z: pruned forward FFT
+// (pass 1 of length L1 over z = L2 n1 + n2, pass 2 of length L2), multiply by
+// the kernel table (Ghat/(2n)^3) with the Parseval energy w(kx) Ghat
+// |rho_hat|^2, inverse FFT keeping z < n.  In place on X.  The pairs of a CTA
+// share its slice of the kernel table (L1 hits after the first pair).
+template <typename R, int N, int NW, int PPC, bool ENERGY_ONLY>
+__global__ void __launch_bounds__(32 * NW, sizeof(R) == 4 ? 3 : 2)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
-        double* __restrict__ epart) {
+        double* __restrict__ epart, int npair) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int W = L < 32 ? L : 32;
   constexpr int M = N + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* tw = reinterpret_cast<C*>(smem_raw);  // [2L]: high parts, then low parts
-  C* twl = tw + L;
-  C* buf = tw + 2 * L;  // [L slots][W]
+  C* tw = reinterpret_cast<C*>(smem_raw);  // w^k [L]
+  C* buf = tw + L;                         // [L slots][W]
+  // this CTA's slice of the kernel table, Gt[kx][kz][ky0 .. ky0 + W), staged
+  // by asynchronous 16-byte copies that overlap the first pass (FP32 with
+  // 16-byte aligned rows; otherwise the values are read from global memory)
+  constexpr bool kStageG = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 && (L * sizeof(R)) % 16 == 0;
+  R* gsm = reinterpret_cast<R*>(buf + L * W);  // [L][W]
   __shared__ double red[NW];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int yb = blockIdx.x, kx = blockIdx.y, p = blockIdx.z;
+  const int yb = blockIdx.x, kx = blockIdx.y;
   const int ky = yb * W + lane;
   const bool valid = lane < W && ky < L;
-  for (int t = tid; t < 2 * L; t += 32 * NW) tw[t] = tw_g[t];
-  C* col = X + (((long long)p * M + kx) * N) * L + (valid ? ky : 0);
-  __syncthreads();
-
-  // forward, pass 1
-  for (int n2 = warp; n2 < L2; n2 += NW) {
-    C v[L1];
-#pragma unroll
-    for (int n1 = 0; n1 < H1; ++n1)
-      v[n1] = valid ? col[(long long)(L2 * n1 + n2) * L] : mkc<C>(R(0), R(0));
-    dft_halfin<L1, -1, true>(v);
-    if (lane < W) {
-      buf[(n2 * L1) * W + lane] = v[0];
-#pragma unroll
-      for (int k1 = 1; k1 < L1; ++k1)
-        buf[(n2 * L1 + k1) * W + lane] = cmul2<true>(v[k1], tw[n2 * k1], twl[n2 * k1]);
+  for (int t = tid; t < L; t += 32 * NW) tw[t] = tw_g[t];
+  const R* __restrict__ Gk = Gs + (long long)kx * L * L + (valid ? ky : 0);
+  if constexpr (kStageG) {
+    constexpr int VPR = 16 / sizeof(R), RPR = W / VPR;  // values / requests per row
+    for (int t = tid; t < L * RPR; t += 32 * NW) {
+      const int kz = t / RPR, c = (t - kz * RPR) * VPR;
+      const int k0 = yb * W + c;  // first ky of the request; L % VPR == 0
+      cp_async16(gsm + kz * W + c, Gs + ((long long)kx * L + kz) * L + (k0 < L ? k0 : 0),
+                 k0 < L ? 16 : 0);
     }
+    cp_async_commit();
   }
-  __syncthreads();
-
-  // forward pass 2, kernel multiply, energy, inverse pass 1
-  const int kyf = ky <= N ? ky : L - ky;
-  const R* __restrict__ Gk = Gs + (long long)kx * M * M + (valid ? kyf : 0);
-  double eacc = 0.0;
-  for (int k1 = warp; k1 < L1; k1 += NW) {
-    C v[L2];
-#pragma unroll
-    for (int n2 = 0; n2 < L2; ++n2)
-      v[n2] = lane < W ? buf[(n2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
-    dft<L2, 1, -1, true>(v);
-    R es = R(0);
-#pragma unroll
-    for (int k2 = 0; k2 < L2; ++k2) {
-      const int kz = k1 + L1 * k2;
-      const int kzf = kz <= N ? kz : L - kz;
-      const R gv = valid ? __ldg(Gk + kzf * M) : R(0);
-      es += gv * (sq(v[k2].x) + sq(v[k2].y));
-      v[k2] = cscale(v[k2], gv);
-    }
-    eacc += (double)es;
-    if constexpr (!ENERGY_ONLY) {
-      dft<L2, 1, 1>(v);
-      if (lane < W) {
-        buf[k1 * W + lane] = v[0];
-#pragma unroll
-        for (int m2 = 1; m2 < L2; ++m2) buf[(m2 * L1 + k1) * W + lane] = cmulc(v[m2], tw[m2 * k1]);
-      }
-    }
-  }
-  if constexpr (!ENERGY_ONLY) {
+  for (int pp = 0; pp < PPC; ++pp) {
+    const int p = blockIdx.z * PPC + pp;
+    if (p >= npair) break;
+    C* col = X + (((long long)p * M + kx) * N) * L + (valid ? ky : 0);
     __syncthreads();
-    // inverse, pass 2: only z = L2 m1 + m2 < n is kept
-    for (int m2 = warp; m2 < L2; m2 += NW) {
+
+    // forward, pass 1
+    for (int n2 = warp; n2 < L2; n2 += NW) {
       C v[L1];
 #pragma unroll
-      for (int k1 = 0; k1 < L1; ++k1)
-        v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
-      dft_halfout<L1, 1>(v);
-      if (valid) {
+      for (int n1 = 0; n1 < H1; ++n1)
+        v[n1] = valid ? col[(long long)(L2 * n1 + n2) * L] : mkc<C>(R(0), R(0));
+      dft_halfin<L1, -1>(v);
+      if (lane < W) {
+        buf[(n2 * L1) * W + lane] = v[0];
 #pragma unroll
-        for (int m1 = 0; m1 < H1; ++m1) col[(long long)(L2 * m1 + m2) * L] = v[m1];
+        for (int k1 = 1; k1 < L1; ++k1)
+          buf[(n2 * L1 + k1) * W + lane] = cmul(v[k1], tw[n2 * k1]);
       }
     }
-  }
-  // Parseval energy of this block (fixed-order reduction)
+    if constexpr (kStageG) cp_async_wait_all();  // own copies done; the barrier publishes all
+    __syncthreads();
+
+    // forward pass 2, kernel multiply, energy, inverse pass 1
+    double eacc = 0.0;
+    for (int k1 = warp; k1 < L1; k1 += NW) {
+      C v[L2];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
-  if (lane == 0) red[warp] = eacc;
-  __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
+      for (int n2 = 0; n2 < L2; ++n2)
+        v[n2] = lane < W ? buf[(n2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
+      dft<L2, 1, -1>(v);
+      R es = R(0);
 #pragma unroll
-    for (int w = 0; w < NW; ++w) s += red[w];
-    const double wk = (kx == 0 || kx == N) ? 1.0 : 2.0;
-    epart[((long long)p * M + kx) * gridDim.x + yb] = wk * s;
+      for (int k2 = 0; k2 < L2; ++k2) {
+        const int kz = k1 + L1 * k2;
+        R gv;
+        if constexpr (kStageG) gv = valid ? gsm[kz * W + lane] : R(0);  // lane < W
+        else gv = valid ? __ldg(Gk + kz * L) : R(0);
+        es += gv * (sq(v[k2].x) + sq(v[k2].y));
+        v[k2] = cscale(v[k2], gv);
+      }
+      eacc += (double)es;
+      if constexpr (!ENERGY_ONLY) {
+        dft<L2, 1, 1>(v);
+        if (lane < W) {
+          buf[k1 * W + lane] = v[0];
+#pragma unroll
+          for (int m2 = 1; m2 < L2; ++m2) buf[(m2 * L1 + k1) * W + lane] = cmulc(v[m2], tw[m2 * k1]);
+        }
+      }
+    }
+    if constexpr (!ENERGY_ONLY) {
+      __syncthreads();
+      // inverse, pass 2: only z = L2 m1 + m2 < n is kept
+      for (int m2 = warp; m2 < L2; m2 += NW) {
+        C v[L1];
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1)
+          v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
+        dft_halfout<L1, 1>(v);
+        if (valid) {
+#pragma unroll
+          for (int m1 = 0; m1 < H1; ++m1) col[(long long)(L2 * m1 + m2) * L] = v[m1];
+        }
+      }
+    }
+    // Parseval energy of this block (fixed-order reduction)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+    if (lane == 0) red[warp] = eacc;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s += red[w];
+      const double wk = (kx == 0 || kx == N) ? 1.0 : 2.0;
+      epart[((long long)p * M + kx) * gridDim.x + yb] = wk * s;
+    }
   }
 }
 
@@ -345,7 +391,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   const int z = blockIdx.x;
   const int p = blockIdx.y;
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
-  for (int t = tid; t < L; t += NT) ti[t] = tw_g[4 * L + 2 * N + t];
+  for (int t = tid; t < L; t += NT) ti[t] = tw_g[2 * L + N + t];
   __syncthreads();
   // y: inverse length-2n FFT per kx row keeping y < n; pass 1 (DFT_L2 over
   // k2, twiddle) from HBM into a row scratch, pass 2 (pruned-output DFT_L1

@@ -33,13 +33,13 @@ const Ops* find_ops(int prec, int n);
 
 constexpr int kNoallocMaxN = EXX_NOALLOC_MAX_N;
 constexpr size_t kSpecElems = (size_t)(kNoallocMaxN + 1) * kNoallocMaxN * 2 * kNoallocMaxN;
-constexpr size_t kKernElems =
-    (size_t)(kNoallocMaxN + 1) * (kNoallocMaxN + 1) * (kNoallocMaxN + 1);
-constexpr int kTwElems = 12 * kNoallocMaxN;  // exx::twiddle_count(n) for n <= max
+// kernel table (exx::kernel_table_bytes(n, 4) / 4 floats for n <= max)
+constexpr size_t kKernElems = (size_t)(kNoallocMaxN + 1) * 2 * kNoallocMaxN * 2 * kNoallocMaxN;
+constexpr int kTwElems = 7 * kNoallocMaxN;  // exx::twiddle_count(n) for n <= max
 constexpr int kEpartElems = (kNoallocMaxN + 1) * ((2 * kNoallocMaxN + 31) / 32);
 
 // Shared scratch of every call on a device (contents persist between calls):
-// the pair's spectrum (complex), the scaled kernel octant, the twiddles, the
+// the pair's spectrum (complex), the kernel table, the twiddles, the
 // column-block energy partials and the pair slot.
 static __device__ __align__(256) float2 g_noalloc_spec[kSpecElems];
 static __device__ __align__(256) float g_noalloc_kern[kKernElems];
@@ -94,7 +94,7 @@ exx_status_t lookup_addresses(DeviceScratch& d) {
   return EXX_OK;
 }
 
-// Kernel spectrum (scaled by 1/(2n)^3, FP32) and twiddles for (n, h, kind),
+// Kernel table (exx::build_kernel_table, FP32) and twiddles for (n, h, kind),
 // built on the host and copied into the arrays; synchronises the stream.
 exx_status_t load_tables(DeviceScratch& d, const exx::Ops* ops, int n, double h, int kind,
                          cudaStream_t st) {
@@ -103,12 +103,13 @@ exx_status_t load_tables(DeviceScratch& d, const exx::Ops* ops, int n, double h,
   if (!exx_host::kernel_spectrum_octant(n, h, kind, 0.0, G.data())) return EXX_ERR_INVALID_ARG;
   const double L = 2.0 * n;
   const double scale = 1.0 / (L * L * L);
-  std::vector<float> Gf(G.size());
-  for (size_t k = 0; k < G.size(); ++k) Gf[k] = (float)(G[k] * scale);
+  std::vector<double> gx(m), gz(2 * (size_t)n);
+  ops->gains(gx.data(), gz.data());
+  std::vector<unsigned char> Gt(exx::kernel_table_bytes(n, sizeof(float)));
+  exx::build_kernel_table<float>(n, G.data(), scale, gx.data(), gz.data(), Gt.data());
   std::vector<float2> tw(exx::twiddle_count(n));
   exx::build_twiddles(n, reinterpret_cast<float*>(tw.data()));
-  cudaError_t e = cudaMemcpyAsync(d.kern, Gf.data(), Gf.size() * sizeof(float),
-                                  cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(d.kern, Gt.data(), Gt.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstddef>
 
+#include "exx_gain.cuh"
 #include "exx_kernels.cuh"
 
 namespace exx {
@@ -18,6 +19,8 @@ struct Ops {
   int nw_b = 0;            // warps per CTA of zconv
   size_t smem_a = 0, smem_b = 0, smem_c = 0;
   cudaError_t (*setup)() = nullptr;
+  // energy gains of the FP32 forward transforms (null for FP64): gx[n+1], gz[2n]
+  void (*gains)(double* gx, double* gz) = nullptr;
   // psi_tab (device array of orbital-array pointers, indexed by the pair's
   // molecule slot) may be null, in which case every pair reads psi
   void (*fwd_xy)(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
@@ -62,35 +65,54 @@ constexpr int zconv_warps(int l2) {
        : (l2 % 5 == 0) ? 5 : 4;
 }
 
-// Twiddle tables of one grid size, packed in one array of complex values;
-// exponent e stands for w^e = exp(-2 pi i e / L), L = 2n:
-//   [0, L)          w^k, high parts; [L, 2L) their low parts (zero in FP64)
-//   [2L, 3L)        TY[k1][n2] = w^(n2 k1), k1 < L1, n2 < L2; [3L, 4L) low parts
-//   [4L, 4L+n)      TX[k1][n2] = w^(2 n2 k1), k1 < X1, n2 < X2; [4L+n, 4L+2n) low
-//   [4L+2n, 5L+2n)  TI[m2][k1] = w^(m2 k1), m2 < L2, k1 < L1 (high parts)
+// Twiddle tables of one grid size, packed in one array of complex values
+// rounded to nearest in the plan's precision; exponent e stands for
+// w^e = exp(-2 pi i e / L), L = 2n:
+//   [0, L)          w^k
+//   [L, 2L)         TY[k1][n2] = w^(n2 k1), k1 < L1, n2 < L2
+//   [2L, 2L+n)      TX[k1][n2] = w^(2 n2 k1), k1 < X1, n2 < X2
+//   [2L+n, 3L+n)    TI[m2][k1] = w^(m2 k1), m2 < L2, k1 < L1
 // The two-dimensional tables put the index that varies across the lanes of
 // the slab kernels' passes fastest, so that their reads are conflict free.
-inline size_t twiddle_count(int n) { return (size_t)12 * n; }
+inline size_t twiddle_count(int n) { return (size_t)7 * n; }
 template <typename R> void build_twiddles(int n, R* out) {
   const int L = 2 * n, L1 = split_l1(L), L2 = L1 ? L / L1 : 1;
   const int X1 = split_x(n), X2 = X1 ? n / X1 : 1;
-  auto put = [&](size_t idx, long e, size_t lo) {
+  auto put = [&](size_t idx, long e) {
     const double a = -M_PI * (double)(e % L) / (double)n;
-    const double c = std::cos(a), s = std::sin(a);
-    out[2 * idx] = (R)c;
-    out[2 * idx + 1] = (R)s;
-    if (lo) {
-      out[2 * (idx + lo)] = (R)(c - (double)(R)c);
-      out[2 * (idx + lo) + 1] = (R)(s - (double)(R)s);
-    }
+    out[2 * idx] = (R)std::cos(a);
+    out[2 * idx + 1] = (R)std::sin(a);
   };
-  for (int k = 0; k < L; ++k) put(k, k, L);
+  for (int k = 0; k < L; ++k) put(k, k);
   for (int k1 = 0; k1 < L1; ++k1)
-    for (int n2 = 0; n2 < L2; ++n2) put(2 * L + k1 * L2 + n2, (long)n2 * k1, L);
+    for (int n2 = 0; n2 < L2; ++n2) put(L + k1 * L2 + n2, (long)n2 * k1);
   for (int k1 = 0; k1 < X1; ++k1)
-    for (int n2 = 0; n2 < X2; ++n2) put(4 * L + k1 * X2 + n2, (long)2 * n2 * k1, n);
+    for (int n2 = 0; n2 < X2; ++n2) put(2 * L + k1 * X2 + n2, (long)2 * n2 * k1);
   for (int m2 = 0; m2 < L2; ++m2)
-    for (int k1 = 0; k1 < L1; ++k1) put(4 * L + 2 * n + m2 * L1 + k1, (long)m2 * k1, 0);
+    for (int k1 = 0; k1 < L1; ++k1) put(2 * L + n + m2 * L1 + k1, (long)m2 * k1);
+}
+
+// Kernel table of zconv (layout in exx_kernels.cuh) from the octant
+// Ghat[kx][kz][ky], k <= n: scale * Ghat / (gx[kx] gz[ky] gz[kz]).  gx, gz are
+// the energy gains |d|^2 of the FP32 forward transforms (exx_gain.cuh; the y
+// and z passes share gz), null for FP64.
+inline size_t kernel_table_bytes(int n, size_t real_size) {
+  return (size_t)(n + 1) * (2 * (size_t)n) * (2 * (size_t)n) * real_size;
+}
+template <typename R>
+void build_kernel_table(int n, const double* octant, double scale, const double* gx,
+                        const double* gz, unsigned char* out) {
+  const size_t m = (size_t)n + 1, L = 2 * (size_t)n;
+  R* G = reinterpret_cast<R*>(out);
+  for (size_t kx = 0; kx < m; ++kx)
+    for (size_t kz = 0; kz < L; ++kz) {
+      const size_t kzf = kz <= (size_t)n ? kz : L - kz;
+      const double c = scale / ((gx ? gx[kx] : 1.0) * (gz ? gz[kz] : 1.0));
+      for (size_t ky = 0; ky < L; ++ky) {
+        const size_t kyf = ky <= (size_t)n ? ky : L - ky;
+        G[(kx * L + kz) * L + ky] = (R)(c / (gz ? gz[ky] : 1.0) * octant[(kx * m + kzf) * m + kyf]);
+      }
+    }
 }
 
 template <typename R, int N> struct OpsImpl {
@@ -101,15 +123,18 @@ template <typename R, int N> struct OpsImpl {
   static constexpr int X1 = split_x(N);
   static constexpr size_t slab = (size_t)(N + 1) * (N + 1) * sizeof(C);
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
-  static constexpr SlabShape SA = slab_shape(slab + (size_t)(2 * L + 2 * N) * sizeof(C), line, true);
+  static constexpr SlabShape SA = slab_shape(slab + (size_t)(L + N) * sizeof(C), line, true);
   static constexpr SlabShape SC = slab_shape(slab + (size_t)2 * L * sizeof(C), line, true);
   static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb;
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
   static constexpr int NW = zconv_warps(L2);
+  static constexpr int PPC = 1;  // pairs per zconv CTA (2 and 4 measured slower at n = 96)
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
-  static constexpr size_t smem_b = ((size_t)2 * L + (size_t)L * W) * sizeof(C);
+  static constexpr bool stage_g = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 && (L * sizeof(R)) % 16 == 0;
+  static constexpr size_t smem_b =
+      ((size_t)L + (size_t)L * W) * sizeof(C) + (stage_g ? (size_t)L * W * sizeof(R) : 0);
   static constexpr bool ok = L1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
 
   static cudaError_t setup() {
@@ -118,10 +143,10 @@ template <typename R, int N> struct OpsImpl {
       e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, false>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, PPC, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, true>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, PPC, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
       return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC>,
@@ -139,13 +164,13 @@ template <typename R, int N> struct OpsImpl {
   static void zconv(void* X, const void* Gs, const void* tw, double* epart, int npair,
                     bool energy_only, cudaStream_t st) {
     if constexpr (ok) {
-      const dim3 grid(NYB, N + 1, npair);
+      const dim3 grid(NYB, N + 1, (npair + PPC - 1) / PPC);
       if (energy_only)
-        k_zconv<R, N, NW, true><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
+        k_zconv<R, N, NW, PPC, true><<<grid, 32 * NW, smem_b, st>>>(
+            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, npair);
       else
-        k_zconv<R, N, NW, false><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
+        k_zconv<R, N, NW, PPC, false><<<grid, 32 * NW, smem_b, st>>>(
+            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, npair);
     }
   }
   static void inv_yx(const void* X, void* V, const void* tw, int npair, cudaStream_t st) {
@@ -165,6 +190,7 @@ template <typename R, int N> struct OpsImpl {
     o.smem_b = smem_b;
     o.smem_c = smem_c;
     o.setup = &setup;
+    if constexpr (ok && sizeof(R) == 4) o.gains = &GainModel<N>::gains;
     o.fwd_xy = &fwd_xy;
     o.zconv = &zconv;
     o.inv_yx = &inv_yx;
