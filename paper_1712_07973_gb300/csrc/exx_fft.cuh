@@ -118,68 +118,21 @@ template <int N, typename F> EXX_HD void sfor(F&& f) {
   sfor_impl(std::make_integer_sequence<int, N>{}, f);
 }
 
-// ------------------------------------------- constant products, compensated
-// FP32 rounding of a twiddle (cos, sin) pair does not preserve its modulus,
-// and an FFT chains several such factors per output: the spectrum comes out
-// shrunk by a systematic ~1e-8 per transform, which a quadratic quantity such
-// as the Parseval energy sum turns into a bias of ~1e-7.  With ACC = true every
-// product by a constant k = kh + kl (kh = fp32(k), kl = fp32(k - kh)) folds the
-// small part into the FMA before the single rounding of the large part, which
-// removes the bias; the remaining rounding error is unbiased.  FP64 ignores ACC.
-template <typename R> struct is_f32 { static constexpr bool value = false; };
-template <> struct is_f32<float> { static constexpr bool value = true; };
-
-// x * k
-template <bool ACC, typename R> EXX_HD R kmul(R x, double k) {
-  if constexpr (ACC && is_f32<R>::value) {
-    const float kh = (float)k;
-    const float kl = (float)(k - (double)kh);
-    return fmaf(x, kh, x * kl);
-  } else {
-    return x * (R)k;
-  }
-}
-// y + x * k
-template <bool ACC, typename R> EXX_HD R kfma(R x, double k, R y) {
-  if constexpr (ACC && is_f32<R>::value) {
-    const float kh = (float)k;
-    const float kl = (float)(k - (double)kh);
-    return fmaf(x, kh, fmaf(x, kl, y));
-  } else {
-    return x * (R)k + y;
-  }
-}
-// a * (c + i s) for constants c, s
-template <bool ACC, typename C> EXX_HD C crot(C a, double c, double s) {
+// ------------------------------------------------------ constant products
+// x * k and y + x * k for a constant k (rounded to the working precision), and
+// a * (c + i s).  In FP32 the rounding of the constants makes each forward
+// transform a fixed map whose per-frequency gain differs from 1 by ~1e-7;
+// the gain is modelled on the host (exx_gain.cuh) and divided out of the
+// kernel table used for the energy.
+template <typename R> EXX_HD R kmul(R x, double k) { return x * (R)k; }
+template <typename R> EXX_HD R kfma(R x, double k, R y) { return x * (R)k + y; }
+template <typename C> EXX_HD C crot(C a, double c, double s) {
   using R = typename creal<C>::type;
-  if constexpr (ACC && is_f32<R>::value) {
-    const float ch = (float)c, cl = (float)(c - (double)ch);
-    const float sh = (float)s, sl = (float)(s - (double)sh);
-    const float lre = fmaf(a.x, cl, -a.y * sl);
-    const float lim = fmaf(a.x, sl, a.y * cl);
-    return mkc<C>(fmaf(a.x, ch, fmaf(-a.y, sh, lre)), fmaf(a.x, sh, fmaf(a.y, ch, lim)));
-  } else {
-    return cmul(a, mkc<C>((R)c, (R)s));
-  }
-}
-// a * (wh + wl) for a runtime twiddle given as high and low parts
-template <bool ACC, typename C> EXX_HD C cmul2(C a, C wh, C wl) {
-  using R = typename creal<C>::type;
-  if constexpr (ACC && is_f32<R>::value) {
-    const float lre = fmaf(a.x, wl.x, -a.y * wl.y);
-    const float lim = fmaf(a.x, wl.y, a.y * wl.x);
-    return mkc<C>(fmaf(a.x, wh.x, fmaf(-a.y, wh.y, lre)), fmaf(a.x, wh.y, fmaf(a.y, wh.x, lim)));
-  } else {
-    return cmul(a, wh);
-  }
-}
-// a * conj(wh + wl)
-template <bool ACC, typename C> EXX_HD C cmulc2(C a, C wh, C wl) {
-  return cmul2<ACC>(a, mkc<C>(wh.x, -wh.y), mkc<C>(wl.x, -wl.y));
+  return cmul(a, mkc<C>((R)c, (R)s));
 }
 
 // a * omega^E, omega = exp(SIGN 2 pi i / P)
-template <int SIGN, int P, int E, bool ACC, typename C> EXX_HD C twmul(C a) {
+template <int SIGN, int P, int E, typename C> EXX_HD C twmul(C a) {
   constexpr long e = pmod(E, P);
   if constexpr (e == 0) {
     return a;
@@ -196,9 +149,9 @@ template <int SIGN, int P, int E, bool ACC, typename C> EXX_HD C twmul(C a) {
     constexpr bool sp = (SIGN * sin2pi(E, P)) > 0;
     const auto re = cp ? (sp ? a.x - a.y : a.x + a.y) : (sp ? -a.x - a.y : -a.x + a.y);
     const auto im = cp ? (sp ? a.y + a.x : a.y - a.x) : (sp ? -a.y + a.x : -a.y - a.x);
-    return mkc<C>(kmul<ACC>(re, r), kmul<ACC>(im, r));
+    return mkc<C>(kmul(re, r), kmul(im, r));
   } else {
-    return crot<ACC>(a, cos2pi(E, P), SIGN * sin2pi(E, P));
+    return crot(a, cos2pi(E, P), SIGN * sin2pi(E, P));
   }
 }
 
@@ -214,7 +167,7 @@ template <int P> struct first_factor {
                                               : P;
 };
 
-template <int P, int S, int SIGN, bool ACC = false, typename C> EXX_HD void dft(C* v);
+template <int P, int S, int SIGN, typename C> EXX_HD void dft(C* v);
 
 template <int S, typename C> EXX_HD void dft2(C* v) {
   C a = v[0], b = v[S];
@@ -222,14 +175,14 @@ template <int S, typename C> EXX_HD void dft2(C* v) {
   v[S] = csub(a, b);
 }
 
-template <int S, int SIGN, bool ACC, typename C> EXX_HD void dft3(C* v) {
+template <int S, int SIGN, typename C> EXX_HD void dft3(C* v) {
   using R = typename creal<C>::type;
   constexpr double s3 = SIGN * 0.86602540378443864676372317075294;
   C a = v[0], b = v[S], c = v[2 * S];
   C t1 = cadd(b, c);
   C t2 = mkc<C>(a.x - R(0.5) * t1.x, a.y - R(0.5) * t1.y);
   C d = csub(b, c);
-  C t3 = mkc<C>(-kmul<ACC>(d.y, s3), kmul<ACC>(d.x, s3));  // i * s3 * (b - c)
+  C t3 = mkc<C>(-kmul(d.y, s3), kmul(d.x, s3));  // i * s3 * (b - c)
   v[0] = cadd(a, t1);
   v[S] = cadd(t2, t3);
   v[2 * S] = csub(t2, t3);
@@ -246,7 +199,7 @@ template <int S, int SIGN, typename C> EXX_HD void dft4(C* v) {
 
 // odd prime P: X_k = x0 + sum_{j=1}^{(P-1)/2} [(x_j + x_{P-j}) cos(2 pi jk/P)
 //                                               + SIGN i (x_j - x_{P-j}) sin(2 pi jk/P)]
-template <int P, int S, int SIGN, bool ACC, typename C> EXX_HD void dft_prime(C* v) {
+template <int P, int S, int SIGN, typename C> EXX_HD void dft_prime(C* v) {
   using R = typename creal<C>::type;
   constexpr int H = (P - 1) / 2;
   C sp[H], sm[H];
@@ -265,10 +218,10 @@ template <int P, int S, int SIGN, bool ACC, typename C> EXX_HD void dft_prime(C*
       constexpr int j = J + 1;
       constexpr double c = cos2pi((long)j * k, P);
       constexpr double s = SIGN * sin2pi((long)j * k, P);
-      re = kfma<ACC>(sp[J].x, c, re);
-      im = kfma<ACC>(sp[J].y, c, im);
-      qre = kfma<ACC>(sm[J].y, -s, qre);  // real part of i * s * sm
-      qim = kfma<ACC>(sm[J].x, s, qim);
+      re = kfma(sp[J].x, c, re);
+      im = kfma(sp[J].y, c, im);
+      qre = kfma(sm[J].y, -s, qre);  // real part of i * s * sm
+      qim = kfma(sm[J].x, s, qim);
     });
     v[k * S] = mkc<C>(re + qre, im + qim);
     v[(P - k) * S] = mkc<C>(re - qre, im - qim);
@@ -277,54 +230,54 @@ template <int P, int S, int SIGN, bool ACC, typename C> EXX_HD void dft_prime(C*
 }
 
 // composite P = A * B (A = first factor): input n = B*n1 + n2, output k1 + A*k2
-template <int P, int S, int SIGN, bool ACC, typename C> EXX_HD void dft_composite(C* v) {
+template <int P, int S, int SIGN, typename C> EXX_HD void dft_composite(C* v) {
   constexpr int A = first_factor<P>::value;
   constexpr int B = P / A;
   // step 1: B DFTs of length A over n1 (stride B*S), in place
-  sfor<B>([&](auto N2) { dft<A, B * S, SIGN, ACC>(v + N2 * S); });
+  sfor<B>([&](auto N2) { dft<A, B * S, SIGN>(v + N2 * S); });
   // twiddle: element at (B*k1 + n2) *= omega_P^{n2 k1}
   sfor<A>([&](auto K1) {
     sfor<B>([&](auto N2) {
       constexpr int idx = (B * K1 + N2) * S;
-      v[idx] = twmul<SIGN, P, (int)(N2 * K1), ACC>(v[idx]);
+      v[idx] = twmul<SIGN, P, (int)(N2 * K1)>(v[idx]);
     });
   });
   // step 2: A DFTs of length B over n2 (contiguous blocks of B)
-  sfor<A>([&](auto K1) { dft<B, S, SIGN, ACC>(v + B * K1 * S); });
+  sfor<A>([&](auto K1) { dft<B, S, SIGN>(v + B * K1 * S); });
   // position (B*k1 + k2) holds X[k1 + A*k2]: transpose to natural order
   C t[P];
   sfor<A>([&](auto K1) { sfor<B>([&](auto K2) { t[K1 + A * K2] = v[(B * K1 + K2) * S]; }); });
   sfor<P>([&](auto I) { v[I * S] = t[I]; });
 }
 
-template <int P, int S, int SIGN, bool ACC, typename C> EXX_HD void dft(C* v) {
+template <int P, int S, int SIGN, typename C> EXX_HD void dft(C* v) {
   if constexpr (P == 1) {
   } else if constexpr (P == 2) {
     dft2<S>(v);
   } else if constexpr (P == 3) {
-    dft3<S, SIGN, ACC>(v);
+    dft3<S, SIGN>(v);
   } else if constexpr (P == 4) {
     dft4<S, SIGN>(v);
   } else if constexpr (P == 5 || P == 7) {
-    dft_prime<P, S, SIGN, ACC>(v);
+    dft_prime<P, S, SIGN>(v);
   } else {
     static_assert(first_factor<P>::value != P, "DFT length with a prime factor > 7");
-    dft_composite<P, S, SIGN, ACC>(v);
+    dft_composite<P, S, SIGN>(v);
   }
 }
 
 // Pruned input: only v[0..P/2) are nonzero (the rest is ignored).  Output all
 // P values in natural order.  X[2k] = DFT_{P/2}(x), X[2k+1] = DFT_{P/2}(x w^j).
-template <int P, int SIGN, bool ACC = false, typename C> EXX_HD void dft_halfin(C* v) {
+template <int P, int SIGN, typename C> EXX_HD void dft_halfin(C* v) {
   static_assert(P % 2 == 0, "pruned DFT needs an even length");
   constexpr int H = P / 2;
   C e[H], o[H];
   sfor<H>([&](auto J) {
     e[J] = v[J];
-    o[J] = twmul<SIGN, P, (int)J, ACC>(v[J]);
+    o[J] = twmul<SIGN, P, (int)J>(v[J]);
   });
-  dft<H, 1, SIGN, ACC>(e);
-  dft<H, 1, SIGN, ACC>(o);
+  dft<H, 1, SIGN>(e);
+  dft<H, 1, SIGN>(o);
   sfor<H>([&](auto K) {
     v[2 * K] = e[K];
     v[2 * K + 1] = o[K];
@@ -333,7 +286,7 @@ template <int P, int SIGN, bool ACC = false, typename C> EXX_HD void dft_halfin(
 
 // Pruned output: all P inputs, only outputs y[0..P/2) are produced (into
 // v[0..P/2)).  y[j] = DFT_{P/2}(x_even)[j] + w^j DFT_{P/2}(x_odd)[j].
-template <int P, int SIGN, bool ACC = false, typename C> EXX_HD void dft_halfout(C* v) {
+template <int P, int SIGN, typename C> EXX_HD void dft_halfout(C* v) {
   static_assert(P % 2 == 0, "pruned DFT needs an even length");
   constexpr int H = P / 2;
   C e[H], o[H];
@@ -341,9 +294,9 @@ template <int P, int SIGN, bool ACC = false, typename C> EXX_HD void dft_halfout
     e[J] = v[2 * J];
     o[J] = v[2 * J + 1];
   });
-  dft<H, 1, SIGN, ACC>(e);
-  dft<H, 1, SIGN, ACC>(o);
-  sfor<H>([&](auto J) { v[J] = cadd(e[J], twmul<SIGN, P, (int)J, ACC>(o[J])); });
+  dft<H, 1, SIGN>(e);
+  dft<H, 1, SIGN>(o);
+  sfor<H>([&](auto J) { v[J] = cadd(e[J], twmul<SIGN, P, (int)J>(o[J])); });
 }
 
 // Four-step split of a line length L = L1 * L2: L1 even (pruning), L1 <= 16,

@@ -63,14 +63,14 @@ template <int N> struct GainModel {
     for (int n2 = 0; n2 < L2; ++n2) {
       C v[L1];
       for (int n1 = 0; n1 < H1; ++n1) v[n1] = in[L2 * n1 + n2];
-      dft_halfin<L1, -1, false>(v);
+      dft_halfin<L1, -1>(v);
       B[n2 * L1] = v[0];
       for (int k1 = 1; k1 < L1; ++k1) B[n2 * L1 + k1] = cmul(v[k1], tw((long)n2 * k1));
     }
     for (int k1 = 0; k1 < L1; ++k1) {
       C v[L2];
       for (int n2 = 0; n2 < L2; ++n2) v[n2] = B[n2 * L1 + k1];
-      dft<L2, 1, -1, false>(v);
+      dft<L2, 1, -1>(v);
       for (int k2 = 0; k2 < L2; ++k2) out[k1 + L1 * k2] = v[k2];
     }
   }
@@ -85,15 +85,15 @@ template <int N> struct GainModel {
         const int m = X2 * n1 + n2;
         v[n1] = raw(2 * m < N ? in[2 * m] : 0.0, 2 * m + 1 < N ? in[2 * m + 1] : 0.0);
       }
-      if constexpr (PX) dft_halfin<X1, -1, false>(v);
-      else dft<X1, 1, -1, false>(v);
+      if constexpr (PX) dft_halfin<X1, -1>(v);
+      else dft<X1, 1, -1>(v);
       Z1[n2 * X1] = v[0];
       for (int k1 = 1; k1 < X1; ++k1) Z1[n2 * X1 + k1] = cmul(v[k1], tw((long)2 * n2 * k1));
     }
     for (int k1 = 0; k1 < X1; ++k1) {
       C v[X2];
       for (int n2 = 0; n2 < X2; ++n2) v[n2] = Z1[n2 * X1 + k1];
-      dft<X2, 1, -1, false>(v);
+      dft<X2, 1, -1>(v);
       for (int k2 = 0; k2 < X2; ++k2) Z[k1 + X1 * k2] = v[k2];
     }
     out[0] = raw(Z[0].x.v + Z[0].y.v, 0.0);

@@ -245,16 +245,19 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 }
 
 // ------------------------------------------------------------------- zconv
-// One CTA per (32 consecutive ky columns, kx, PPC consecutive pairs); lane =
-// column, warps share the sub-DFTs of each pass.  Along z: pruned forward FFT
-// (pass 1 of length L1 over z = L2 n1 + n2, pass 2 of length L2), multiply by
-// the kernel table (Ghat/(2n)^3) with the Parseval energy w(kx) Ghat
-// |rho_hat|^2, inverse FFT keeping z < n.  In place on X.  The pairs of a CTA
-// share its slice of the kernel table (L1 hits after the first pair).
-template <typename R, int N, int NW, int PPC, bool ENERGY_ONLY>
+// One CTA per (32 consecutive ky columns, kx, pair); lane = column, warps
+// share the sub-DFTs of each pass.  Along z: pruned forward FFT (pass 1 of
+// length L1 over z = L2 n1 + n2, pass 2 of length L2), multiply by the kernel
+// table (Ghat/(2n)^3) with the Parseval energy w(kx) Ghat |rho_hat|^2, inverse
+// FFT keeping z < n.  In place on X.  STAGE: the CTA's slice of the kernel
+// table, Gt[kx][kz][ky0 .. ky0 + W), is copied to shared memory by
+// asynchronous 16-byte copies that overlap the first pass (FP32 rows aligned
+// to 16 bytes, and only where it costs no occupancy); otherwise the values
+// are read from global memory in the second pass.
+template <typename R, int N, int NW, bool STAGE, bool ENERGY_ONLY>
 __global__ void __launch_bounds__(32 * NW, sizeof(R) == 4 ? 3 : 2)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
-        double* __restrict__ epart, int npair) {
+        double* __restrict__ epart) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int W = L < 32 ? L : 32;
@@ -262,20 +265,17 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);  // w^k [L]
   C* buf = tw + L;                         // [L slots][W]
-  // this CTA's slice of the kernel table, Gt[kx][kz][ky0 .. ky0 + W), staged
-  // by asynchronous 16-byte copies that overlap the first pass (FP32 with
-  // 16-byte aligned rows; otherwise the values are read from global memory)
-  constexpr bool kStageG = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 && (L * sizeof(R)) % 16 == 0;
-  R* gsm = reinterpret_cast<R*>(buf + L * W);  // [L][W]
+  R* gsm = reinterpret_cast<R*>(buf + L * W);  // [L][W] (STAGE)
   __shared__ double red[NW];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int yb = blockIdx.x, kx = blockIdx.y;
+  const int yb = blockIdx.x, kx = blockIdx.y, p = blockIdx.z;
   const int ky = yb * W + lane;
   const bool valid = lane < W && ky < L;
   for (int t = tid; t < L; t += 32 * NW) tw[t] = tw_g[t];
   const R* __restrict__ Gk = Gs + (long long)kx * L * L + (valid ? ky : 0);
-  if constexpr (kStageG) {
+  if constexpr (STAGE) {
+    static_assert((W * sizeof(R)) % 16 == 0 && (L * sizeof(R)) % 16 == 0, "unaligned rows");
     constexpr int VPR = 16 / sizeof(R), RPR = W / VPR;  // values / requests per row
     for (int t = tid; t < L * RPR; t += 32 * NW) {
       const int kz = t / RPR, c = (t - kz * RPR) * VPR;
@@ -285,84 +285,80 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
     }
     cp_async_commit();
   }
-  for (int pp = 0; pp < PPC; ++pp) {
-    const int p = blockIdx.z * PPC + pp;
-    if (p >= npair) break;
-    C* col = X + (((long long)p * M + kx) * N) * L + (valid ? ky : 0);
-    __syncthreads();
+  C* col = X + (((long long)p * M + kx) * N) * L + (valid ? ky : 0);
+  __syncthreads();
 
-    // forward, pass 1
-    for (int n2 = warp; n2 < L2; n2 += NW) {
+  // forward, pass 1
+  for (int n2 = warp; n2 < L2; n2 += NW) {
+    C v[L1];
+#pragma unroll
+    for (int n1 = 0; n1 < H1; ++n1)
+      v[n1] = valid ? col[(long long)(L2 * n1 + n2) * L] : mkc<C>(R(0), R(0));
+    dft_halfin<L1, -1>(v);
+    if (lane < W) {
+      buf[(n2 * L1) * W + lane] = v[0];
+#pragma unroll
+      for (int k1 = 1; k1 < L1; ++k1)
+        buf[(n2 * L1 + k1) * W + lane] = cmul(v[k1], tw[n2 * k1]);
+    }
+  }
+  if constexpr (STAGE) cp_async_wait_all();  // own copies done; the barrier publishes all
+  __syncthreads();
+
+  // forward pass 2, kernel multiply, energy, inverse pass 1
+  double eacc = 0.0;
+  for (int k1 = warp; k1 < L1; k1 += NW) {
+    C v[L2];
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2)
+      v[n2] = lane < W ? buf[(n2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
+    dft<L2, 1, -1>(v);
+    R es = R(0);
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) {
+      const int kz = k1 + L1 * k2;
+      R gv;
+      if constexpr (STAGE) gv = valid ? gsm[kz * W + lane] : R(0);  // lane < W
+      else gv = valid ? __ldg(Gk + kz * L) : R(0);
+      es += gv * (sq(v[k2].x) + sq(v[k2].y));
+      v[k2] = cscale(v[k2], gv);
+    }
+    eacc += (double)es;
+    if constexpr (!ENERGY_ONLY) {
+      dft<L2, 1, 1>(v);
+      if (lane < W) {
+        buf[k1 * W + lane] = v[0];
+#pragma unroll
+        for (int m2 = 1; m2 < L2; ++m2) buf[(m2 * L1 + k1) * W + lane] = cmulc(v[m2], tw[m2 * k1]);
+      }
+    }
+  }
+  if constexpr (!ENERGY_ONLY) {
+    __syncthreads();
+    // inverse, pass 2: only z = L2 m1 + m2 < n is kept
+    for (int m2 = warp; m2 < L2; m2 += NW) {
       C v[L1];
 #pragma unroll
-      for (int n1 = 0; n1 < H1; ++n1)
-        v[n1] = valid ? col[(long long)(L2 * n1 + n2) * L] : mkc<C>(R(0), R(0));
-      dft_halfin<L1, -1>(v);
-      if (lane < W) {
-        buf[(n2 * L1) * W + lane] = v[0];
+      for (int k1 = 0; k1 < L1; ++k1)
+        v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
+      dft_halfout<L1, 1>(v);
+      if (valid) {
 #pragma unroll
-        for (int k1 = 1; k1 < L1; ++k1)
-          buf[(n2 * L1 + k1) * W + lane] = cmul(v[k1], tw[n2 * k1]);
+        for (int m1 = 0; m1 < H1; ++m1) col[(long long)(L2 * m1 + m2) * L] = v[m1];
       }
     }
-    if constexpr (kStageG) cp_async_wait_all();  // own copies done; the barrier publishes all
-    __syncthreads();
-
-    // forward pass 2, kernel multiply, energy, inverse pass 1
-    double eacc = 0.0;
-    for (int k1 = warp; k1 < L1; k1 += NW) {
-      C v[L2];
+  }
+  // Parseval energy of this block (fixed-order reduction)
 #pragma unroll
-      for (int n2 = 0; n2 < L2; ++n2)
-        v[n2] = lane < W ? buf[(n2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
-      dft<L2, 1, -1>(v);
-      R es = R(0);
+  for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+  if (lane == 0) red[warp] = eacc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
 #pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) {
-        const int kz = k1 + L1 * k2;
-        R gv;
-        if constexpr (kStageG) gv = valid ? gsm[kz * W + lane] : R(0);  // lane < W
-        else gv = valid ? __ldg(Gk + kz * L) : R(0);
-        es += gv * (sq(v[k2].x) + sq(v[k2].y));
-        v[k2] = cscale(v[k2], gv);
-      }
-      eacc += (double)es;
-      if constexpr (!ENERGY_ONLY) {
-        dft<L2, 1, 1>(v);
-        if (lane < W) {
-          buf[k1 * W + lane] = v[0];
-#pragma unroll
-          for (int m2 = 1; m2 < L2; ++m2) buf[(m2 * L1 + k1) * W + lane] = cmulc(v[m2], tw[m2 * k1]);
-        }
-      }
-    }
-    if constexpr (!ENERGY_ONLY) {
-      __syncthreads();
-      // inverse, pass 2: only z = L2 m1 + m2 < n is kept
-      for (int m2 = warp; m2 < L2; m2 += NW) {
-        C v[L1];
-#pragma unroll
-        for (int k1 = 0; k1 < L1; ++k1)
-          v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
-        dft_halfout<L1, 1>(v);
-        if (valid) {
-#pragma unroll
-          for (int m1 = 0; m1 < H1; ++m1) col[(long long)(L2 * m1 + m2) * L] = v[m1];
-        }
-      }
-    }
-    // Parseval energy of this block (fixed-order reduction)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
-    if (lane == 0) red[warp] = eacc;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) s += red[w];
-      const double wk = (kx == 0 || kx == N) ? 1.0 : 2.0;
-      epart[((long long)p * M + kx) * gridDim.x + yb] = wk * s;
-    }
+    for (int w = 0; w < NW; ++w) s += red[w];
+    const double wk = (kx == 0 || kx == N) ? 1.0 : 2.0;
+    epart[((long long)p * M + kx) * gridDim.x + yb] = wk * s;
   }
 }
 

@@ -129,12 +129,16 @@ template <typename R, int N> struct OpsImpl {
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
   static constexpr int NW = zconv_warps(L2);
-  static constexpr int PPC = 1;  // pairs per zconv CTA (2 and 4 measured slower at n = 96)
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
-  static constexpr bool stage_g = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 && (L * sizeof(R)) % 16 == 0;
-  static constexpr size_t smem_b =
-      ((size_t)L + (size_t)L * W) * sizeof(C) + (stage_g ? (size_t)L * W * sizeof(R) : 0);
+  // zconv: twiddles + column buffer, plus the staged kernel-table slice when
+  // its rows are 16-byte aligned and three CTAs (the FP32 launch bound) still
+  // fit in an SM's 228 KB of shared memory
+  static constexpr size_t smem_b0 = ((size_t)L + (size_t)L * W) * sizeof(C);
+  static constexpr size_t smem_g = (size_t)L * W * sizeof(R);
+  static constexpr bool stage_g = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 &&
+                                  (L * sizeof(R)) % 16 == 0 && 3 * (smem_b0 + smem_g + 1024) <= 228 * 1024;
+  static constexpr size_t smem_b = smem_b0 + (stage_g ? smem_g : 0);
   static constexpr bool ok = L1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
 
   static cudaError_t setup() {
@@ -143,10 +147,10 @@ template <typename R, int N> struct OpsImpl {
       e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, PPC, false>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, stage_g, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, PPC, true>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, stage_g, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
       return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC>,
@@ -164,13 +168,13 @@ template <typename R, int N> struct OpsImpl {
   static void zconv(void* X, const void* Gs, const void* tw, double* epart, int npair,
                     bool energy_only, cudaStream_t st) {
     if constexpr (ok) {
-      const dim3 grid(NYB, N + 1, (npair + PPC - 1) / PPC);
+      const dim3 grid(NYB, N + 1, npair);
       if (energy_only)
-        k_zconv<R, N, NW, PPC, true><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, npair);
+        k_zconv<R, N, NW, stage_g, true><<<grid, 32 * NW, smem_b, st>>>(
+            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
       else
-        k_zconv<R, N, NW, PPC, false><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, npair);
+        k_zconv<R, N, NW, stage_g, false><<<grid, 32 * NW, smem_b, st>>>(
+            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
     }
   }
   static void inv_yx(const void* X, void* V, const void* tw, int npair, cudaStream_t st) {

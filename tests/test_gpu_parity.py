@@ -201,6 +201,10 @@ def test_fp32_workload_64_orbitals_n96_full_size(torch_dev):
     assert abs(E - g["E_x"]) <= 1e-6, (E, g["E_x"])
     assert abs(Ee - g["E_x"]) <= 1e-6
     assert np.max(np.abs(Eij - np.array(g["E_ij"]))) <= 1e-6
+    # the systematic FP32 bias (rounded FFT constants shrink the spectrum by
+    # ~1e-7 relative; 1.8e-6 Ha here without correction) is divided out of the
+    # kernel table: what remains is rounding noise, measured 8e-8 Ha
+    assert abs(E - g["E_x"]) <= 3e-7, (E, g["E_x"])
     pts = np.array(g["sample_points"])
     samples = vx[pts[:, 0], pts[:, 1], pts[:, 2], pts[:, 3]]
     ref = np.array(g["vx_samples"])
