@@ -162,7 +162,7 @@ def algorithmic_bytes(n, N, T, rs=4):
     for npair, ti, tj, diag in tile_list(N, T):
         orbs = ti if diag else ti + tj
         tot["fwd_xy"] += orbs * n3 * rs + npair * spec
-        tot["zconv"] += 2 * npair * spec + (n + 1) ** 3 * rs
+        tot["zconv"] += 2 * npair * spec + (n + 1) * (2 * n) ** 2 * rs
         tot["inv_yx"] += npair * spec + npair * n3 * rs
         tot["accum"] += npair * n3 * rs + orbs * n3 * rs + 2 * orbs * n3 * 8
     return tot

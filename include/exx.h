@@ -200,7 +200,7 @@ exx_status_t exx_profile_read(exx_plan_t plan, double* ms, long long* launches, 
  *   psi            device, float [norb][n][n][n]; orbitals i and j are used.
  *   E_dev          device, one double, receives E_ij (no host copy, no sync).
  * Scratch is a set of file-scope device arrays sized for EXX_NOALLOC_MAX_N
- * (about 18 MB, held by every GPU that loads the library until the process
+ * (about 29 MB, held by every GPU that loads the library until the process
  * exits).  n > EXX_NOALLOC_MAX_N returns EXX_ERR_NOT_SUPPORTED, as does a grid
  * without compiled kernels.  The first call on a device looks up the arrays'
  * device addresses (cudaGetSymbolAddress), and any call whose (n, h, kernel)
