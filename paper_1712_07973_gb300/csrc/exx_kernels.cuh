@@ -37,6 +37,16 @@ __host__ __device__ constexpr int split_x(int n) {
   return 0;
 }
 
+// Slab of the slab kernels: rows r = 0..n (k_x) of SP = n + 1 complex values
+// (columns y), row r starting at srow(r) = r SP + r / X1.  The extra slot
+// every X1 rows skews the rows n2 X1 + k1 that the 16 lanes of an x-pass unit
+// group touch (consecutive n2) onto distinct banks: the bank of (row, y) is
+// 2 (n2 (X1 SP + 1) + k1 SP + y) mod 32, and X1 SP + 1 is odd.
+__host__ __device__ constexpr int slab_elems(int n) {
+  return (n + 1) * (n + 1) + n / split_x(n) + 1;
+}
+template <int SP, int X1> __device__ __forceinline__ int srow(int r) { return r * SP + r / X1; }
+
 // Padded scratch layout of one line in the [a][k1] form of the four-step:
 // slot(a, k1) = a * (L1 + 1) + k1; the line stride is odd so that lines of
 // different units land on different banks.
@@ -101,7 +111,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   // consecutive lanes (consecutive n2) read consecutive entries
   C* ty = reinterpret_cast<C*>(smem_raw);
   C* tx = ty + L;
-  C* Sl = tx + N;  // [(N+1)][SP]
+  C* Sl = tx + N;  // slab, rows srow(r)
 
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
@@ -133,7 +143,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       for (int n1 = XIN; n1 < X1; ++n1) v[n1] = mkc<C>(R(0), R(0));
       dft<X1, 1, -1>(v);
     }
-    C* col = Sl + (n2 * X1) * SP + y;
+    C* col = Sl + srow<SP, X1>(n2 * X1) + y;  // rows n2 X1 + k1 at col[k1 SP]
     col[0] = v[0];
 #pragma unroll
     for (int k1 = 1; k1 < X1; ++k1)  // omega_n^{n2 k1} = omega_2n^{2 n2 k1}
@@ -145,10 +155,10 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
     const int k1 = u / N, y = u - k1 * N;
     C v[X2];
 #pragma unroll
-    for (int n2 = 0; n2 < X2; ++n2) v[n2] = Sl[(n2 * X1 + k1) * SP + y];
+    for (int n2 = 0; n2 < X2; ++n2) v[n2] = Sl[srow<SP, X1>(n2 * X1 + k1) + y];
     dft<X2, 1, -1>(v);
 #pragma unroll
-    for (int k2 = 0; k2 < X2; ++k2) Sl[(k1 + X1 * k2) * SP + y] = v[k2];
+    for (int k2 = 0; k2 < X2; ++k2) Sl[srow<SP, X1>(k1 + X1 * k2) + y] = v[k2];
   }
   __syncthreads();
   // split: X[k] = E[k] + w^k O[k], X[n-k] = conj(E[k] - w^k O[k]), with
@@ -158,22 +168,24 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
     if (k == 0) {
       const C z0 = Sl[y];
       Sl[y] = mkc<C>(z0.x + z0.y, R(0));
-      Sl[N * SP + y] = mkc<C>(z0.x - z0.y, R(0));
+      Sl[srow<SP, X1>(N) + y] = mkc<C>(z0.x - z0.y, R(0));
     } else if (2 * k == N) {
-      const C zk = Sl[k * SP + y];
-      Sl[k * SP + y] = mkc<C>(zk.x, -zk.y);
+      const C zk = Sl[srow<SP, X1>(k) + y];
+      Sl[srow<SP, X1>(k) + y] = mkc<C>(zk.x, -zk.y);
     } else {
       C xk, xm;
-      split_step(Sl[k * SP + y], Sl[(N - k) * SP + y], __ldg(tw_g + k), xk, xm);  // uniform k
-      Sl[k * SP + y] = xk;
-      Sl[(N - k) * SP + y] = xm;
+      C* rk = Sl + srow<SP, X1>(k) + y;
+      C* rm = Sl + srow<SP, X1>(N - k) + y;
+      split_step(*rk, *rm, __ldg(tw_g + k), xk, xm);  // uniform k
+      *rk = xk;
+      *rm = xm;
     }
   }
   __syncthreads();
   // y: pruned length-2n FFT per kx row; pass 1 (DFT_L1 over n1 < L1/2, then
   // the twiddle) into a row scratch in the padded [n2][k1] layout, pass 2
   // (DFT_L2 over n2) straight to HBM
-  C* S = Sl + (N + 1) * SP;
+  C* S = Sl + slab_elems(N);
   if constexpr (Q == 0) {
     // warp-owned: each warp transforms two kx rows at a time (one per half
     // warp) in its own scratch, synchronising with __syncwarp only
@@ -185,7 +197,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       const bool rv = kx <= N;
       for (int n2 = c; n2 < L2; n2 += 16) {
         if (rv) {
-          const C* row = Sl + kx * SP;
+          const C* row = Sl + srow<SP, X1>(kx);
           C v[L1];
 #pragma unroll
           for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
@@ -217,7 +229,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       // the scratch writes stride the (odd) line length, both bank-conflict free
       for (int u = tid; u < nr * L2; u += NT) {
         const int n2 = u / nr, r = u - n2 * nr;
-        const C* row = Sl + (r0 + r) * SP;
+        const C* row = Sl + srow<SP, X1>(r0 + r);
         C v[L1];
 #pragma unroll
         for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
@@ -381,7 +393,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);  // w^k, high parts [L]
   C* ti = tw + L;                          // TI[m2][k1] = w^(m2 k1) [L] (see fwd_xy)
-  C* Sl = ti + L;                          // [(N+1)][SP]
+  C* Sl = ti + L;                          // slab, rows srow(r) (see fwd_xy)
 
   const int tid = threadIdx.x;
   const int z = blockIdx.x;
@@ -392,7 +404,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   // y: inverse length-2n FFT per kx row keeping y < n; pass 1 (DFT_L2 over
   // k2, twiddle) from HBM into a row scratch, pass 2 (pruned-output DFT_L1
   // over k1) into the slab
-  C* S = Sl + (N + 1) * SP;
+  C* S = Sl + slab_elems(N);
   if constexpr (Q == 0) {
     // warp-owned: two kx rows per warp (one per half warp), own scratch
     constexpr int NWP = NT / 32;
@@ -420,7 +432,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
 #pragma unroll
           for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
           dft_halfout<L1, 1>(v);
-          C* row = Sl + kx * SP;
+          C* row = Sl + srow<SP, X1>(kx);
 #pragma unroll
           for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
         }
@@ -451,7 +463,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
 #pragma unroll
         for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
         dft_halfout<L1, 1>(v);
-        C* row = Sl + (r0 + r) * SP;
+        C* row = Sl + srow<SP, X1>(r0 + r);
 #pragma unroll
         for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
       }
@@ -462,18 +474,21 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   for (int u = tid; u < N * (N / 2 + 1); u += NT) {
     const int k = u / N, y = u - k * N;
     if (k == 0) {
-      const R x0 = Sl[y].x, xn = Sl[N * SP + y].x;
+      const R x0 = Sl[y].x, xn = Sl[srow<SP, X1>(N) + y].x;
       Sl[y] = mkc<C>(x0 + xn, x0 - xn);
     } else if (2 * k == N) {
-      const C xk = Sl[k * SP + y];
-      Sl[k * SP + y] = mkc<C>(R(2) * xk.x, R(-2) * xk.y);
+      C* rk = Sl + srow<SP, X1>(k) + y;
+      const C xk = *rk;
+      *rk = mkc<C>(R(2) * xk.x, R(-2) * xk.y);
     } else {
-      const C xk = Sl[k * SP + y], xm = Sl[(N - k) * SP + y];
+      C* rk = Sl + srow<SP, X1>(k) + y;
+      C* rm = Sl + srow<SP, X1>(N - k) + y;
+      const C xk = *rk, xm = *rm;
       const C e = mkc<C>(xk.x + xm.x, xk.y - xm.y);
       const C d = mkc<C>(xk.x - xm.x, xk.y + xm.y);
       const C o = cmulc(d, tw[k]);
-      Sl[k * SP + y] = mkc<C>(e.x - o.y, e.y + o.x);
-      Sl[(N - k) * SP + y] = mkc<C>(e.x + o.y, o.x - e.y);
+      *rk = mkc<C>(e.x - o.y, e.y + o.x);
+      *rm = mkc<C>(e.x + o.y, o.x - e.y);
     }
   }
   __syncthreads();
@@ -482,11 +497,11 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
     const int k1 = u / N, y = u - k1 * N;
     C v[X2];
 #pragma unroll
-    for (int k2 = 0; k2 < X2; ++k2) v[k2] = Sl[(k1 + X1 * k2) * SP + y];
+    for (int k2 = 0; k2 < X2; ++k2) v[k2] = Sl[srow<SP, X1>(k1 + X1 * k2) + y];
     dft<X2, 1, 1>(v);
-    Sl[k1 * SP + y] = v[0];
+    Sl[srow<SP, X1>(k1) + y] = v[0];
 #pragma unroll
-    for (int m2 = 1; m2 < X2; ++m2) Sl[(m2 * X1 + k1) * SP + y] = cmulc(v[m2], tw[2 * m2 * k1]);
+    for (int m2 = 1; m2 < X2; ++m2) Sl[srow<SP, X1>(m2 * X1 + k1) + y] = cmulc(v[m2], tw[2 * m2 * k1]);
   }
   __syncthreads();
   // x inverse, pass 2: units (y, m2), m2 fastest (coalesced writes of row y)
@@ -495,7 +510,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
     const int y = u / X2, m2 = u - y * X2;
     C v[X1];
 #pragma unroll
-    for (int k1 = 0; k1 < X1; ++k1) v[k1] = Sl[(m2 * X1 + k1) * SP + y];
+    for (int k1 = 0; k1 < X1; ++k1) v[k1] = Sl[srow<SP, X1>(m2 * X1 + k1) + y];
     if constexpr (PX) dft_halfout<X1, 1>(v);
     else dft<X1, 1, 1>(v);
     R* row = Vz + (long long)y * N;

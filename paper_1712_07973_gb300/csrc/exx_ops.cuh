@@ -121,7 +121,7 @@ template <typename R, int N> struct OpsImpl {
   static constexpr int L1 = split_l1(L);
   static constexpr int L2 = L1 ? L / L1 : 1;
   static constexpr int X1 = split_x(N);
-  static constexpr size_t slab = (size_t)(N + 1) * (N + 1) * sizeof(C);
+  static constexpr size_t slab = X1 ? (size_t)slab_elems(N) * sizeof(C) : 0;
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
   static constexpr SlabShape SA = slab_shape(slab + (size_t)(L + N) * sizeof(C), line, true);
   static constexpr SlabShape SC = slab_shape(slab + (size_t)2 * L * sizeof(C), line, true);
