@@ -408,7 +408,7 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   const size_t cs = 2 * rs;
   // kernel table (scaled by 1/(2n)^3; for FP32 with the forward transforms'
   // gains divided out) and twiddle tables (exx_ops.cuh)
-  std::vector<unsigned char> gbuf(exx::kernel_table_bytes(n, rs)), twbuf(exx::twiddle_count(n) * cs);
+  std::vector<unsigned char> gbuf(exx::kernel_table_bytes(n, rs, ops->table_fold_y)), twbuf(exx::twiddle_count(n) * cs);
   std::vector<double> gx, gz;
   if (ops->gains) {
     gx.resize(m);
@@ -416,10 +416,10 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
     ops->gains(gx.data(), gz.data());
   }
   if (precision == EXX_FP64) {
-    exx::build_kernel_table<double>(n, Gh.data(), scale, nullptr, nullptr, gbuf.data());
+    exx::build_kernel_table<double>(n, ops->table_fold_y, Gh.data(), scale, nullptr, nullptr, gbuf.data());
     exx::build_twiddles(n, reinterpret_cast<double*>(twbuf.data()));
   } else {
-    exx::build_kernel_table<float>(n, Gh.data(), scale, gx.empty() ? nullptr : gx.data(),
+    exx::build_kernel_table<float>(n, ops->table_fold_y, Gh.data(), scale, gx.empty() ? nullptr : gx.data(),
                                    gz.empty() ? nullptr : gz.data(), gbuf.data());
     exx::build_twiddles(n, reinterpret_cast<float*>(twbuf.data()));
   }

@@ -421,8 +421,8 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
     const double L = 2.0 * g.n, scale = 1.0 / (L * L * L);
     std::vector<double> gx(m), gz(2 * (size_t)g.n);
     g.ops->gains(gx.data(), gz.data());
-    std::vector<unsigned char> gf(exx::kernel_table_bytes(g.n, sizeof(float)));
-    exx::build_kernel_table<float>(g.n, Gh.data(), scale, gx.data(), gz.data(), gf.data());
+    std::vector<unsigned char> gf(exx::kernel_table_bytes(g.n, sizeof(float), g.ops->table_fold_y));
+    exx::build_kernel_table<float>(g.n, g.ops->table_fold_y, Gh.data(), scale, gx.data(), gz.data(), gf.data());
     std::vector<float> tw(2 * exx::twiddle_count(g.n));
     exx::build_twiddles(g.n, tw.data());
     if (!balloc(b, &g.Gs, gf.size()) || !balloc(b, &g.tw, tw.size() * sizeof(float))) {

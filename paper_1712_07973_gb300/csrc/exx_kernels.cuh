@@ -71,7 +71,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // kx <= n, kz, ky < 2n, the scaled kernel spectrum divided by the energy
 // gains |dx(kx)|^2 |dy(ky)|^2 |dz(kz)|^2 of the FP32 forward transforms (1 in
 // FP64).  Stored unfolded (Ghat is even in ky and kz) so that the gains,
-// which are not, are divided out in the table itself.
+// which are not, are divided out in the table itself.  For large grids
+// (FOLDY) the table keeps ky folded, Gt[kx][kz][min(ky, 2n - ky)] without the
+// y gain, which follows as cy[ky] = 1 / |dy(ky)|^2 (double, at
+// ktab_cy_offset) and is applied to each column's energy: half the size,
+// for L2 residency.
+__host__ __device__ constexpr size_t ktab_cy_offset(int n, size_t rs) {
+  return ((size_t)(n + 1) * (2 * n) * (n + 1) * rs + 7) / 8 * 8;
+}
 
 // One step of the split of the complex length-n spectrum Z of the (even, odd)
 // sample pairs into the Hermitian half spectrum X of the real length-2n line:
@@ -266,8 +273,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 // asynchronous 16-byte copies that overlap the first pass (FP32 rows aligned
 // to 16 bytes, and only where it costs no occupancy); otherwise the values
 // are read from global memory in the second pass.
-template <typename R, int N, int NW, bool STAGE, bool ENERGY_ONLY>
-__global__ void __launch_bounds__(32 * NW, sizeof(R) == 4 ? 3 : 2)
+template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool ENERGY_ONLY>
+__global__ void __launch_bounds__(32 * NW, MINB)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
         double* __restrict__ epart) {
   using C = cplx<R>;
@@ -285,7 +292,16 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   const int ky = yb * W + lane;
   const bool valid = lane < W && ky < L;
   for (int t = tid; t < L; t += 32 * NW) tw[t] = tw_g[t];
-  const R* __restrict__ Gk = Gs + (long long)kx * L * L + (valid ? ky : 0);
+  constexpr int GR = FOLDY ? N + 1 : L;  // table row length
+  const int kyt = FOLDY ? (ky <= N ? ky : L - ky) : ky;
+  const R* __restrict__ Gk = Gs + (long long)kx * L * GR + (valid ? kyt : 0);
+  double cyl = 1.0;
+  if constexpr (FOLDY) {
+    static_assert(!STAGE, "staging reads unfolded rows");
+    if (valid)
+      cyl = reinterpret_cast<const double*>(reinterpret_cast<const unsigned char*>(Gs) +
+                                            ktab_cy_offset(N, sizeof(R)))[ky];
+  }
   if constexpr (STAGE) {
     static_assert((W * sizeof(R)) % 16 == 0 && (L * sizeof(R)) % 16 == 0, "unaligned rows");
     constexpr int VPR = 16 / sizeof(R), RPR = W / VPR;  // values / requests per row
@@ -331,7 +347,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
       const int kz = k1 + L1 * k2;
       R gv;
       if constexpr (STAGE) gv = valid ? gsm[kz * W + lane] : R(0);  // lane < W
-      else gv = valid ? __ldg(Gk + kz * L) : R(0);
+      else gv = valid ? __ldg(Gk + kz * GR) : R(0);
       es += gv * (sq(v[k2].x) + sq(v[k2].y));
       v[k2] = cscale(v[k2], gv);
     }
@@ -361,6 +377,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
     }
   }
   // Parseval energy of this block (fixed-order reduction)
+  if constexpr (FOLDY) eacc *= cyl;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
   if (lane == 0) red[warp] = eacc;

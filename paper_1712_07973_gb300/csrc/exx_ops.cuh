@@ -21,6 +21,7 @@ struct Ops {
   cudaError_t (*setup)() = nullptr;
   // energy gains of the FP32 forward transforms (null for FP64): gx[n+1], gz[2n]
   void (*gains)(double* gx, double* gz) = nullptr;
+  bool table_fold_y = false;  // kernel-table layout (build_kernel_table)
   // psi_tab (device array of orbital-array pointers, indexed by the pair's
   // molecule slot) may be null, in which case every pair reads psi
   void (*fwd_xy)(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
@@ -93,26 +94,33 @@ template <typename R> void build_twiddles(int n, R* out) {
 }
 
 // Kernel table of zconv (layout in exx_kernels.cuh) from the octant
-// Ghat[kx][kz][ky], k <= n: scale * Ghat / (gx[kx] gz[ky] gz[kz]).  gx, gz are
+// Ghat[kx][kz][ky], k <= n: scale * Ghat / (gx[kx] gz[ky] gz[kz]), or with
+// fold_y the ky-folded rows without gz[ky] followed by 1 / gz[ky].  gx, gz are
 // the energy gains |d|^2 of the FP32 forward transforms (exx_gain.cuh; the y
 // and z passes share gz), null for FP64.
-inline size_t kernel_table_bytes(int n, size_t real_size) {
+inline size_t kernel_table_bytes(int n, size_t real_size, bool fold_y) {
+  if (fold_y) return ktab_cy_offset(n, real_size) + 2 * (size_t)n * sizeof(double);
   return (size_t)(n + 1) * (2 * (size_t)n) * (2 * (size_t)n) * real_size;
 }
 template <typename R>
-void build_kernel_table(int n, const double* octant, double scale, const double* gx,
+void build_kernel_table(int n, bool fold_y, const double* octant, double scale, const double* gx,
                         const double* gz, unsigned char* out) {
-  const size_t m = (size_t)n + 1, L = 2 * (size_t)n;
+  const size_t m = (size_t)n + 1, L = 2 * (size_t)n, row = fold_y ? m : L;
   R* G = reinterpret_cast<R*>(out);
   for (size_t kx = 0; kx < m; ++kx)
     for (size_t kz = 0; kz < L; ++kz) {
       const size_t kzf = kz <= (size_t)n ? kz : L - kz;
       const double c = scale / ((gx ? gx[kx] : 1.0) * (gz ? gz[kz] : 1.0));
-      for (size_t ky = 0; ky < L; ++ky) {
+      for (size_t ky = 0; ky < row; ++ky) {
         const size_t kyf = ky <= (size_t)n ? ky : L - ky;
-        G[(kx * L + kz) * L + ky] = (R)(c / (gz ? gz[ky] : 1.0) * octant[(kx * m + kzf) * m + kyf]);
+        const double cy = (fold_y || !gz) ? 1.0 : 1.0 / gz[ky];
+        G[(kx * L + kz) * row + ky] = (R)(c * cy * octant[(kx * m + kzf) * m + kyf]);
       }
     }
+  if (fold_y) {
+    double* cy = reinterpret_cast<double*>(out + ktab_cy_offset(n, sizeof(R)));
+    for (size_t k = 0; k < L; ++k) cy[k] = gz ? 1.0 / gz[k] : 1.0;
+  }
 }
 
 template <typename R, int N> struct OpsImpl {
@@ -139,6 +147,11 @@ template <typename R, int N> struct OpsImpl {
   static constexpr bool stage_g = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 &&
                                   (L * sizeof(R)) % 16 == 0 && 3 * (smem_b0 + smem_g + 1024) <= 228 * 1024;
   static constexpr size_t smem_b = smem_b0 + (stage_g ? smem_g : 0);
+  // CTAs per SM the zconv register budget is sized for: three where shared
+  // memory allows (FP32), else two
+  static constexpr int MINB_B = (sizeof(R) == 4 && 3 * (smem_b + 1024) <= 228 * 1024) ? 3 : 2;
+  // ky-folded kernel table where the unfolded one would exceed 24 MB
+  static constexpr bool fold_y = !stage_g && (size_t)(N + 1) * (2 * N) * (2 * N) * sizeof(R) > (24u << 20);
   static constexpr bool ok = L1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
 
   static cudaError_t setup() {
@@ -147,10 +160,10 @@ template <typename R, int N> struct OpsImpl {
       e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, stage_g, false>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, stage_g, true>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
       return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC>,
@@ -170,10 +183,10 @@ template <typename R, int N> struct OpsImpl {
     if constexpr (ok) {
       const dim3 grid(NYB, N + 1, npair);
       if (energy_only)
-        k_zconv<R, N, NW, stage_g, true><<<grid, 32 * NW, smem_b, st>>>(
+        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, true><<<grid, 32 * NW, smem_b, st>>>(
             static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
       else
-        k_zconv<R, N, NW, stage_g, false><<<grid, 32 * NW, smem_b, st>>>(
+        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, false><<<grid, 32 * NW, smem_b, st>>>(
             static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
     }
   }
@@ -194,6 +207,7 @@ template <typename R, int N> struct OpsImpl {
     o.smem_b = smem_b;
     o.smem_c = smem_c;
     o.setup = &setup;
+    o.table_fold_y = fold_y;
     if constexpr (ok && sizeof(R) == 4) o.gains = &GainModel<N>::gains;
     o.fwd_xy = &fwd_xy;
     o.zconv = &zconv;
