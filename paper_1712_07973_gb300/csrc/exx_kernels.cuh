@@ -23,6 +23,8 @@
 // Layouts: psi[o][z][y][x]; X[p][kx][z][ky] complex; V[p][z][y][x].
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "exx_fft.cuh"
 
 namespace exx {
@@ -37,13 +39,14 @@ __host__ __device__ constexpr int split_x(int n) {
   return 0;
 }
 
-// Slab of the slab kernels: rows r = 0..n (k_x) of SP = n + 1 complex values
-// (columns y), row r starting at srow(r) = r SP + r / X1.  The extra slot
-// every X1 rows skews the rows n2 X1 + k1 that the 16 lanes of an x-pass unit
-// group touch (consecutive n2) onto distinct banks: the bank of (row, y) is
-// 2 (n2 (X1 SP + 1) + k1 SP + y) mod 32, and X1 SP + 1 is odd.
-__host__ __device__ constexpr int slab_elems(int n) {
-  return (n + 1) * (n + 1) + n / split_x(n) + 1;
+// Slab of the slab kernels: rows r = 0..n (k_x) of SP = ny + 1 complex values
+// (columns y; ny = n, or n / 2 per CTA of a two-CTA cluster), row r starting
+// at srow(r) = r SP + r / X1.  The extra slot every X1 rows skews the rows
+// n2 X1 + k1 that the 16 lanes of an x-pass unit group touch (consecutive n2)
+// onto distinct banks: the bank of (row, y) is 2 (n2 (X1 SP + 1) + k1 SP + y)
+// mod 32, and X1 SP + 1 is odd.
+__host__ __device__ constexpr int slab_elems(int n, int ny) {
+  return (n + 1) * (ny + 1) + n / split_x(n) + 1;
 }
 template <int SP, int X1> __device__ __forceinline__ int srow(int r) { return r * SP + r / X1; }
 
@@ -101,7 +104,11 @@ template <typename C> EXX_HD void split_step(C zk, C zm, C w, C& xk, C& xm) {
 // Hermitian half spectrum X[k], k = 0..n (row n is the Nyquist row).  y: the
 // pruned length-2n FFT per kx row, written to HBM as X[p][kx][z][ky].  Q = 0:
 // warp-owned y passes (two rows per warp); Q > 0: CTA-wide batches of Q rows.
-template <typename R, int N, int NT, int MINB, int Q>
+// CL = 2 (large grids): a cluster of two CTAs per (z-slab, pair), CTA c holding
+// the columns y in [c n/2, (c+1) n/2) of every row; the x passes stay local,
+// the y passes of a CTA's rows read the other half of each row from the peer's
+// shared memory (distributed shared memory).
+template <typename R, int N, int NT, int MINB, int Q, int CL>
 __global__ void __launch_bounds__(NT, MINB)
 k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
          const int4* __restrict__ pairs, cplx<R>* __restrict__ X, const cplx<R>* __restrict__ tw_g,
@@ -111,7 +118,9 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   constexpr int X1 = split_x(N), X2 = N / X1;
   constexpr bool PX = (N % 2) == 0;  // pruned x input
   constexpr int XIN = PX ? X1 / 2 : X1;
-  constexpr int SP = N + 1;
+  constexpr int NY = N / CL, SP = NY + 1;
+  constexpr int NB = CL == 1 ? H1 : NY / L2;  // y = L2 n1 + n2 lies in half n1 / NB
+  static_assert(CL == 1 || (Q == 0 && N % 2 == 0 && NY % L2 == 0), "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // twiddle tables (packed layout of build_twiddles): TY[k1][n2] = w^(n2 k1)
   // for the y pass and TX[k1][n2] = w^(2 n2 k1) for the x pass, so that
@@ -121,7 +130,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   C* Sl = tx + N;  // slab, rows srow(r)
 
   const int tid = threadIdx.x;
-  const int z = blockIdx.x;
+  const int z = blockIdx.x / CL, c = blockIdx.x % CL;  // c: rank in the cluster
+  const int y0 = c * NY;
   const int p = blockIdx.y;
   const int4 pr = pairs[p];  // (i, j, pair id, molecule slot)
   const R* psi = psi_tab ? psi_tab[pr.w] : psi0;
@@ -130,11 +140,12 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   for (int t = tid; t < L + N; t += NT) ty[t] = tw_g[L + t];
   __syncthreads();
 
-  // x, pass 1: units (y, n2), n2 fastest (coalesced reads of row y)
-  for (int u = tid; u < N * X2; u += NT) {
-    const int y = u / X2, n2 = u - y * X2;
-    const R* ri = pi + y * N;
-    const R* rj = pj + y * N;
+  // x, pass 1: units (y, n2), n2 fastest (coalesced reads of row y); slab
+  // column y - y0
+  for (int u = tid; u < NY * X2; u += NT) {
+    const int yl = u / X2, n2 = u - yl * X2;
+    const R* ri = pi + (y0 + yl) * N;
+    const R* rj = pj + (y0 + yl) * N;
     C v[X1];
 #pragma unroll
     for (int n1 = 0; n1 < XIN; ++n1) {
@@ -150,7 +161,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       for (int n1 = XIN; n1 < X1; ++n1) v[n1] = mkc<C>(R(0), R(0));
       dft<X1, 1, -1>(v);
     }
-    C* col = Sl + srow<SP, X1>(n2 * X1) + y;  // rows n2 X1 + k1 at col[k1 SP]
+    C* col = Sl + srow<SP, X1>(n2 * X1) + yl;  // rows n2 X1 + k1 at col[k1 SP]
     col[0] = v[0];
 #pragma unroll
     for (int k1 = 1; k1 < X1; ++k1)  // omega_n^{n2 k1} = omega_2n^{2 n2 k1}
@@ -158,8 +169,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   }
   __syncthreads();
   // x, pass 2: units (y, k1), y fastest; in place, natural order Z[k] at row k
-  for (int u = tid; u < N * X1; u += NT) {
-    const int k1 = u / N, y = u - k1 * N;
+  for (int u = tid; u < NY * X1; u += NT) {
+    const int k1 = u / NY, y = u - k1 * NY;
     C v[X2];
 #pragma unroll
     for (int n2 = 0; n2 < X2; ++n2) v[n2] = Sl[srow<SP, X1>(n2 * X1 + k1) + y];
@@ -170,8 +181,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   __syncthreads();
   // split: X[k] = E[k] + w^k O[k], X[n-k] = conj(E[k] - w^k O[k]), with
   // E = (Z[k] + conj Z[n-k]) / 2, O = (Z[k] - conj Z[n-k]) / (2i), w = omega_2n
-  for (int u = tid; u < N * (N / 2 + 1); u += NT) {
-    const int k = u / N, y = u - k * N;
+  for (int u = tid; u < NY * (N / 2 + 1); u += NT) {
+    const int k = u / NY, y = u - k * NY;
     if (k == 0) {
       const C z0 = Sl[y];
       Sl[y] = mkc<C>(z0.x + z0.y, R(0));
@@ -188,26 +199,39 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       *rm = xm;
     }
   }
-  __syncthreads();
+  // the two halves of each row (columns below / above n/2): with CL = 2 this
+  // CTA's slab and the peer's
+  const C* h0 = Sl;
+  const C* h1 = Sl;
+  if constexpr (CL == 2) {
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    const C* peer = cl.map_shared_rank(Sl, c ^ 1);
+    h0 = c == 0 ? Sl : peer;
+    h1 = c == 0 ? peer : Sl;
+    cl.sync();  // both halves transformed along x
+  } else {
+    __syncthreads();
+  }
   // y: pruned length-2n FFT per kx row; pass 1 (DFT_L1 over n1 < L1/2, then
   // the twiddle) into a row scratch in the padded [n2][k1] layout, pass 2
   // (DFT_L2 over n2) straight to HBM
-  C* S = Sl + slab_elems(N);
+  C* S = Sl + slab_elems(N, NY);
   if constexpr (Q == 0) {
     // warp-owned: each warp transforms two kx rows at a time (one per half
-    // warp) in its own scratch, synchronising with __syncwarp only
+    // warp) in its own scratch, synchronising with __syncwarp only; the rows
+    // go round-robin over the warps of the cluster
     constexpr int NWP = NT / 32;
-    const int lane = tid & 31, hr = lane >> 4, c = lane & 15;
+    const int lane = tid & 31, hr = lane >> 4, cl16 = lane & 15;
     C* Sw = S + ((tid >> 5) * 2 + hr) * Scr<L1, L2>::line;
-    for (int r0 = 2 * (tid >> 5); r0 <= N; r0 += 2 * NWP) {
+    for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 <= N; r0 += 2 * NWP * CL) {
       const int kx = r0 + hr;
       const bool rv = kx <= N;
-      for (int n2 = c; n2 < L2; n2 += 16) {
+      for (int n2 = cl16; n2 < L2; n2 += 16) {
         if (rv) {
-          const C* row = Sl + srow<SP, X1>(kx);
+          const int rb = srow<SP, X1>(kx);
           C v[L1];
 #pragma unroll
-          for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
+          for (int n1 = 0; n1 < H1; ++n1) v[n1] = (n1 < NB ? h0 : h1)[rb + L2 * (n1 % NB) + n2];
           dft_halfin<L1, -1>(v);
           C* o = Sw + n2 * Scr<L1, L2>::row;
           o[0] = v[0];
@@ -216,18 +240,20 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
         }
       }
       __syncwarp();
-      if (rv && c < L1) {
-        const C* q = Sw + c;
+      if (rv && cl16 < L1) {
+        const C* q = Sw + cl16;
         C v[L2];
 #pragma unroll
         for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
         dft<L2, 1, -1>(v);
-        C* out = X + (((long long)p * (N + 1) + kx) * N + z) * L + c;
+        C* out = X + (((long long)p * (N + 1) + kx) * N + z) * L + cl16;
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
       }
       __syncwarp();
     }
+    // the peer may still be reading this CTA's half
+    if constexpr (CL == 2) cooperative_groups::this_cluster().sync();
   } else {
     // CTA-wide batches of Q rows
     for (int r0 = 0; r0 <= N; r0 += Q) {
@@ -398,7 +424,9 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 // Z[k] = E'[k] + i O'[k] (E' = X[k] + conj X[n-k], O' = (X[k] - conj X[n-k])
 // w^-k), whose inverse FFT (in place in column y) gives the even and odd
 // samples of the real line: V[2m] = Re, V[2m+1] = Im, kept for x < n.
-template <typename R, int N, int NT, int MINB, int Q>
+// CL = 2: two-CTA cluster as in fwd_xy; a CTA's y passes write the other half
+// of each row into the peer's slab, then each CTA transforms its own columns.
+template <typename R, int N, int NT, int MINB, int Q, int CL>
 __global__ void __launch_bounds__(NT, MINB)
 k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __restrict__ tw_g) {
   using C = cplx<R>;
@@ -406,57 +434,72 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   constexpr int X1 = split_x(N), X2 = N / X1;
   constexpr bool PX = (N % 2) == 0;
   constexpr int XOUT = PX ? X1 / 2 : X1;
-  constexpr int SP = N + 1;
+  constexpr int NY = N / CL, SP = NY + 1;
+  constexpr int NB = CL == 1 ? H1 : NY / L2;  // y = L2 m1 + m2 lies in half m1 / NB
+  static_assert(CL == 1 || (Q == 0 && N % 2 == 0 && NY % L2 == 0), "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);  // w^k, high parts [L]
   C* ti = tw + L;                          // TI[m2][k1] = w^(m2 k1) [L] (see fwd_xy)
   C* Sl = ti + L;                          // slab, rows srow(r) (see fwd_xy)
 
   const int tid = threadIdx.x;
-  const int z = blockIdx.x;
+  const int z = blockIdx.x / CL, c = blockIdx.x % CL;  // c: rank in the cluster
+  const int y0 = c * NY;
   const int p = blockIdx.y;
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
   for (int t = tid; t < L; t += NT) ti[t] = tw_g[2 * L + N + t];
-  __syncthreads();
+  C* h0 = Sl;  // row halves (see fwd_xy)
+  C* h1 = Sl;
+  if constexpr (CL == 2) {
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    C* peer = cl.map_shared_rank(Sl, c ^ 1);
+    h0 = c == 0 ? Sl : peer;
+    h1 = c == 0 ? peer : Sl;
+    cl.sync();  // the peer has started (its shared memory may be written)
+  } else {
+    __syncthreads();
+  }
   // y: inverse length-2n FFT per kx row keeping y < n; pass 1 (DFT_L2 over
   // k2, twiddle) from HBM into a row scratch, pass 2 (pruned-output DFT_L1
   // over k1) into the slab
-  C* S = Sl + slab_elems(N);
+  C* S = Sl + slab_elems(N, NY);
   if constexpr (Q == 0) {
-    // warp-owned: two kx rows per warp (one per half warp), own scratch
+    // warp-owned: two kx rows per warp (one per half warp), own scratch; the
+    // rows go round-robin over the warps of the cluster
     constexpr int NWP = NT / 32;
-    const int lane = tid & 31, hr = lane >> 4, c = lane & 15;
+    const int lane = tid & 31, hr = lane >> 4, cl16 = lane & 15;
     C* Sw = S + ((tid >> 5) * 2 + hr) * Scr<L1, L2>::line;
-    for (int r0 = 2 * (tid >> 5); r0 <= N; r0 += 2 * NWP) {
+    for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 <= N; r0 += 2 * NWP * CL) {
       const int kx = r0 + hr;
       const bool rv = kx <= N;
-      if (rv && c < L1) {
-        const C* in = X + (((long long)p * (N + 1) + kx) * N + z) * L + c;
+      if (rv && cl16 < L1) {
+        const C* in = X + (((long long)p * (N + 1) + kx) * N + z) * L + cl16;
         C v[L2];
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
         dft<L2, 1, 1>(v);
-        C* q = Sw + c;
+        C* q = Sw + cl16;
         q[0] = v[0];
 #pragma unroll
-        for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], ti[m2 * L1 + c]);
+        for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], ti[m2 * L1 + cl16]);
       }
       __syncwarp();
-      for (int m2 = c; m2 < L2; m2 += 16) {
+      for (int m2 = cl16; m2 < L2; m2 += 16) {
         if (rv) {
           const C* q = Sw + m2 * Scr<L1, L2>::row;
           C v[L1];
 #pragma unroll
           for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
           dft_halfout<L1, 1>(v);
-          C* row = Sl + srow<SP, X1>(kx);
+          const int rb = srow<SP, X1>(kx);
 #pragma unroll
-          for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
+          for (int m1 = 0; m1 < H1; ++m1) (m1 < NB ? h0 : h1)[rb + L2 * (m1 % NB) + m2] = v[m1];
         }
       }
       __syncwarp();
     }
-    __syncthreads();
+    if constexpr (CL == 2) cooperative_groups::this_cluster().sync();  // both halves written
+    else __syncthreads();
   } else {
     for (int r0 = 0; r0 <= N; r0 += Q) {
       const int nr = min(Q, N + 1 - r0);
@@ -488,8 +531,8 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
     }
   }
   // fold the half spectrum into Z (units (y, k), k = 0..n/2, y fastest)
-  for (int u = tid; u < N * (N / 2 + 1); u += NT) {
-    const int k = u / N, y = u - k * N;
+  for (int u = tid; u < NY * (N / 2 + 1); u += NT) {
+    const int k = u / NY, y = u - k * NY;
     if (k == 0) {
       const R x0 = Sl[y].x, xn = Sl[srow<SP, X1>(N) + y].x;
       Sl[y] = mkc<C>(x0 + xn, x0 - xn);
@@ -510,8 +553,8 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   }
   __syncthreads();
   // x inverse, pass 1: units (y, k1), y fastest; in place over rows k1 + X1 k2
-  for (int u = tid; u < N * X1; u += NT) {
-    const int k1 = u / N, y = u - k1 * N;
+  for (int u = tid; u < NY * X1; u += NT) {
+    const int k1 = u / NY, y = u - k1 * NY;
     C v[X2];
 #pragma unroll
     for (int k2 = 0; k2 < X2; ++k2) v[k2] = Sl[srow<SP, X1>(k1 + X1 * k2) + y];
@@ -523,14 +566,14 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   __syncthreads();
   // x inverse, pass 2: units (y, m2), m2 fastest (coalesced writes of row y)
   R* Vz = V + ((long long)p * N + z) * N * N;
-  for (int u = tid; u < N * X2; u += NT) {
+  for (int u = tid; u < NY * X2; u += NT) {
     const int y = u / X2, m2 = u - y * X2;
     C v[X1];
 #pragma unroll
     for (int k1 = 0; k1 < X1; ++k1) v[k1] = Sl[srow<SP, X1>(m2 * X1 + k1) + y];
     if constexpr (PX) dft_halfout<X1, 1>(v);
     else dft<X1, 1, 1>(v);
-    R* row = Vz + (long long)y * N;
+    R* row = Vz + (long long)(y0 + y) * N;
 #pragma unroll
     for (int m1 = 0; m1 < XOUT; ++m1) {
       const int m = X2 * m1 + m2;

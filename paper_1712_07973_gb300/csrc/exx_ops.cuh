@@ -34,31 +34,62 @@ struct Ops {
 constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation of one CTA
 
 // Launch shape of the slab kernels (fwd_xy, inv_yx): shared memory = fixed
-// part (slab + twiddles) + y-pass scratch.  Preferred: warp-owned y passes
-// (q = 0), two scratch rows per warp, as two CTAs of 320 threads per SM when
-// asked for and they fit in half an SM, else one CTA of 640.  Otherwise
-// CTA-wide batches of q rows.  Measured at n = 96 (64 orbitals): warp-owned
-// y passes with two CTAs per SM take fwd_xy from 13.3 to 13.0 ms and inv_yx
-// from 13.5 to 11.1 ms per exx_apply.
+// part (slab + twiddles) + y-pass scratch.  In order of preference:
+//   warp-owned y passes (q = 0, two scratch rows per warp) as two CTAs of 320
+//   threads per SM when asked for and they fit in half an SM, else one CTA
+//   of 640;
+//   the same with the slab split over a two-CTA cluster (cl = 2, half the
+//   columns per CTA; fixed2 is its fixed part), when allowed;
+//   CTA-wide batches of q rows.
+// Measured at n = 96 (64 orbitals): warp-owned y passes with two CTAs per SM
+// take fwd_xy from 13.3 to 13.0 ms and inv_yx from 13.5 to 11.1 ms per
+// exx_apply.
 struct SlabShape {
-  int q, nt, minb;
+  int q, nt, minb, cl;
   size_t smem;
   bool fits;
 };
-constexpr SlabShape slab_shape(size_t fixed, size_t line, bool prefer_two) {
+constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_t line,
+                               bool prefer_two) {
   const size_t half = 113 * 1024;
-  if (prefer_two && fixed + 20 * line <= half) return SlabShape{0, 320, 2, fixed + 20 * line, true};
-  if (fixed + 40 * line <= kSmemPerCTA) return SlabShape{0, 640, 1, fixed + 40 * line, true};
+  if (prefer_two && fixed + 20 * line <= half) return SlabShape{0, 320, 2, 1, fixed + 20 * line, true};
+  if (fixed + 40 * line <= kSmemPerCTA) return SlabShape{0, 640, 1, 1, fixed + 40 * line, true};
+  if (split_ok && fixed2 + 40 * line <= kSmemPerCTA)
+    return SlabShape{0, 640, 1, 2, fixed2 + 40 * line, true};
   if (prefer_two && fixed + 8 * line <= half) {
     size_t q = (half - fixed) / line;
     q = q > 32 ? 32 : q;
-    return SlabShape{(int)q, 320, 2, fixed + q * line, true};
+    return SlabShape{(int)q, 320, 2, 1, fixed + q * line, true};
   }
-  if (fixed + line > kSmemPerCTA) return SlabShape{1, 640, 1, fixed + line, false};
+  if (fixed + line > kSmemPerCTA) return SlabShape{1, 640, 1, 1, fixed + line, false};
   size_t q = (kSmemPerCTA - fixed) / line;
   q = q > 64 ? 64 : q;
-  return SlabShape{(int)q, 640, 1, fixed + q * line, true};
+  return SlabShape{(int)q, 640, 1, 1, fixed + q * line, true};
 }
+
+// Launch of a slab kernel; CL > 1 launches (CL, 1, 1) thread-block clusters.
+template <int CL, typename... KArgs, typename... Args>
+inline void launch_slab(void (*kern)(KArgs...), dim3 grid, int nt, size_t smem, cudaStream_t st,
+                        Args... args) {
+  if constexpr (CL == 1) {
+    kern<<<grid, nt, smem, st>>>(args...);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+  }
+}
+
 // zconv warps: a count that divides the L2-long passes when possible (12 for
 // L2 = 12 measured 4% faster than 6 at n = 96)
 constexpr int zconv_warps(int l2) {
@@ -129,12 +160,18 @@ template <typename R, int N> struct OpsImpl {
   static constexpr int L1 = split_l1(L);
   static constexpr int L2 = L1 ? L / L1 : 1;
   static constexpr int X1 = split_x(N);
-  static constexpr size_t slab = X1 ? (size_t)slab_elems(N) * sizeof(C) : 0;
+  static constexpr size_t slab = X1 ? (size_t)slab_elems(N, N) * sizeof(C) : 0;
+  // two-CTA split: half the columns per CTA (the y-pass index split must fall
+  // on a whole number of length-L2 groups)
+  static constexpr bool split_ok = X1 && L1 && N % 2 == 0 && (N / 2) % L2 == 0;
+  static constexpr size_t slab2 = split_ok ? (size_t)slab_elems(N, N / 2) * sizeof(C) : 0;
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
-  static constexpr SlabShape SA = slab_shape(slab + (size_t)(L + N) * sizeof(C), line, true);
-  static constexpr SlabShape SC = slab_shape(slab + (size_t)2 * L * sizeof(C), line, true);
-  static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb;
-  static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb;
+  static constexpr SlabShape SA = slab_shape(slab + (size_t)(L + N) * sizeof(C),
+                                             slab2 + (size_t)(L + N) * sizeof(C), split_ok, line, true);
+  static constexpr SlabShape SC = slab_shape(slab + (size_t)2 * L * sizeof(C),
+                                             slab2 + (size_t)2 * L * sizeof(C), split_ok, line, true);
+  static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb, CL_A = SA.cl;
+  static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb, CL_C = SC.cl;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
   static constexpr int NW = zconv_warps(L2);
   static constexpr int W = L < 32 ? L : 32;
@@ -157,7 +194,7 @@ template <typename R, int N> struct OpsImpl {
   static cudaError_t setup() {
     if constexpr (ok) {
       cudaError_t e;
-      e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA>,
+      e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
       if (e != cudaSuccess) return e;
       e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, false>,
@@ -166,7 +203,7 @@ template <typename R, int N> struct OpsImpl {
       e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC>,
+      return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC, CL_C>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
     }
     return cudaErrorNotSupported;
@@ -174,9 +211,10 @@ template <typename R, int N> struct OpsImpl {
   static void fwd_xy(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
                      void* X, const void* tw, long long n3, cudaStream_t st) {
     if constexpr (ok)
-      k_fwd_xy<R, N, NT_A, MINB_A, QA><<<dim3(N, npair), NT_A, smem_a, st>>>(
-          static_cast<const R*>(psi), reinterpret_cast<const R* const*>(psi_tab), pairs,
-          static_cast<C*>(X), static_cast<const C*>(tw), n3);
+      launch_slab<CL_A>(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A>, dim3(N * CL_A, npair), NT_A,
+                        smem_a, st, static_cast<const R*>(psi),
+                        reinterpret_cast<const R* const*>(psi_tab), pairs, static_cast<C*>(X),
+                        static_cast<const C*>(tw), n3);
   }
   static void zconv(void* X, const void* Gs, const void* tw, double* epart, int npair,
                     bool energy_only, cudaStream_t st) {
@@ -192,8 +230,9 @@ template <typename R, int N> struct OpsImpl {
   }
   static void inv_yx(const void* X, void* V, const void* tw, int npair, cudaStream_t st) {
     if constexpr (ok)
-      k_inv_yx<R, N, NT_C, MINB_C, QC><<<dim3(N, npair), NT_C, smem_c, st>>>(
-          static_cast<const C*>(X), static_cast<R*>(V), static_cast<const C*>(tw));
+      launch_slab<CL_C>(k_inv_yx<R, N, NT_C, MINB_C, QC, CL_C>, dim3(N * CL_C, npair), NT_C,
+                        smem_c, st, static_cast<const C*>(X), static_cast<R*>(V),
+                        static_cast<const C*>(tw));
   }
   static Ops make() {
     Ops o;

@@ -214,6 +214,26 @@ def test_fp32_workload_64_orbitals_n96_full_size(torch_dev):
     assert np.allclose(norms, g["vx_norm2"], rtol=1e-5)
 
 
+def test_fp64_workload_64_orbitals_n96_two_cta_slabs(torch_dev):
+    # the FP64 path at n = 96 splits each z-slab over a two-CTA cluster (its
+    # slab does not fit one SM's shared memory); against the stored oracle run
+    path = os.path.join(GOLDEN, "c2_fp32_n96_N64.json")
+    if not os.path.exists(path):
+        pytest.skip("golden values not generated")
+    with open(path) as fh:
+        g = json.load(fh)
+    r, psi = synth.workload("c2_fp32_n96_N64")
+    occ = np.full(r.norb, r.occupation)
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, r.alpha, r.h, "fp64")
+    assert abs(E - g["E_x"]) <= 1e-10 * abs(g["E_x"]), (E, g["E_x"])
+    assert abs(Ee - g["E_x"]) <= 1e-10 * abs(g["E_x"])
+    assert np.max(np.abs(Eij - np.array(g["E_ij"]))) <= 1e-10 * np.max(np.abs(g["E_ij"]))
+    pts = np.array(g["sample_points"])
+    samples = vx[pts[:, 0], pts[:, 1], pts[:, 2], pts[:, 3]]
+    ref = np.array(g["vx_samples"])
+    assert np.max(np.abs(samples - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
 def test_misaligned_caller_pointers(torch_dev):
     # orbitals and output that start 4 bytes past an aligned address take the
     # scalar path of the accumulation and must give the same result
