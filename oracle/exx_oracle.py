@@ -37,6 +37,12 @@ Readings where the paper is silent (each is also listed in the design doc):
   [z, y, x] with x fastest.
 * Occupations are used exactly as passed (no sum over spin channels).
 * E_ij = h^3 * sum_m rho_ij[m] V_ij[m] (rectangle-rule quadrature on the mesh).
+* Periodic boundary conditions (the paper's own H2O and UO2 runs, Sec. 3, are
+  periodic; Sec. 2.1.2 only states that other boundary conditions use other
+  Green's functions): the n^3 cell of side n h repeats, no padding, and
+  V_hat(k) = 4 pi rho_hat(k) / |k|^2 for the band-limited density with the
+  k = 0 term removed (a neutralising background), |k|^2 from the signed
+  frequencies 2 pi m / (n h), |m| <= n/2.
 
 Precision: FP64 throughout.
 """
@@ -55,6 +61,7 @@ __all__ = [
     "sinc_kernel_g1d",
     "kernel_real_space",
     "kernel_spectrum",
+    "kernel_spectrum_periodic",
     "poisson",
     "direct_sum_potential",
     "pair_list",
@@ -194,9 +201,26 @@ def kernel_spectrum(G):
     return np.ascontiguousarray(Ghat.real)
 
 
+def kernel_spectrum_periodic(n, h):
+    """Periodic Coulomb spectrum 4 pi / |k|^2 (k = 0 removed) on the n^3 cell,
+    in scipy's rfftn layout (n, n, n//2 + 1) (see the module header)."""
+    m = np.fft.fftfreq(n, d=1.0 / n)  # signed integer frequencies
+    mx = np.arange(n // 2 + 1, dtype=np.float64)
+    k2 = (2.0 * math.pi / (n * h)) ** 2 * (m[:, None, None] ** 2 + m[None, :, None] ** 2
+                                             + mx[None, None, :] ** 2)
+    with np.errstate(divide="ignore"):
+        G = np.where(k2 > 0, 4.0 * math.pi / np.where(k2 > 0, k2, 1.0), 0.0)
+    return G
+
+
 def poisson(rho, Ghat):
-    """V = G * rho (aperiodic) through the zero-padded 2n FFT (Sec. 2.1.2)."""
+    """V = G * rho.  A spectrum of the padded (2n)^3 grid (kernel_spectrum)
+    gives the aperiodic convolution through the zero-padded FFT (Sec. 2.1.2);
+    one of the n^3 grid (kernel_spectrum_periodic) the periodic solution."""
     n = rho.shape[0]
+    if Ghat.shape[0] == n:
+        return np.ascontiguousarray(sfft.irfftn(sfft.rfftn(rho, workers=-1) * Ghat, s=rho.shape,
+                                                workers=-1))
     pad = np.zeros((2 * n,) * 3, dtype=np.float64)
     pad[:n, :n, :n] = rho
     V = sfft.irfftn(sfft.rfftn(pad, workers=-1) * Ghat, s=(2 * n,) * 3, workers=-1)
