@@ -344,7 +344,7 @@ def test_periodic_gaussian_madelung_constant():
     Ls, Es = np.array(Ls), np.array(Es)
     A = np.stack([-0.5 / Ls, 1.0 / Ls ** 3], axis=1)
     (xi, c), *_ = np.linalg.lstsq(A, Es - 1.0 / (2 * sig * math.sqrt(math.pi)), rcond=None)
-    assert xi == pytest.approx(2.837297479, abs=2e-4), (xi, c)
+    assert xi == pytest.approx(2.837297479, abs=1e-5), (xi, c)
 
 
 def test_periodic_exchange_invariants():
