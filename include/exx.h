@@ -64,10 +64,15 @@ typedef enum {
   EXX_KERNEL_SINC = 0,    /* band-limited free-space kernel (default): exact for
                              densities band-limited to the grid's Brillouin zone */
   EXX_KERNEL_HOCKNEY = 1, /* point-sampled h^3/|r|, cell-averaged origin; O(h^2)  */
-  EXX_KERNEL_ERFC = 2     /* band-limited short-range kernel erfc(omega r)/r of
+  EXX_KERNEL_ERFC = 2,    /* band-limited short-range kernel erfc(omega r)/r of
                              screened hybrids (HSE-type; Sec. 3 notes that only
                              the Poisson filter changes); needs omega > 0 and
                              exx_plan_create_desc                                 */
+  EXX_KERNEL_PERIODIC = 3 /* periodic boundary conditions on the n^3 cell of side
+                             n h (the paper's own runs, Sec. 3, are periodic):
+                             V_hat = 4 pi rho_hat / |k|^2 with k = 0 removed, no
+                             padding; n even, n in {8,12,16,24,32,48,64,96,128,
+                             192} (FP64 up to 128)                                */
 } exx_kernel_t;
 
 /* Plan flags (bitwise or). */
@@ -310,7 +315,9 @@ exx_status_t exx_plan_destroy(exx_plan_t plan);
  * kernel, Ghat[k] = sum_d G~[d] exp(-i pi k.d / n) for k in [0, n]^3 (one
  * octant; Ghat is real and even per axis), unscaled.  omega is used by
  * EXX_KERNEL_ERFC only.  out_host holds (n+1)^3 doubles, index
- * (kz*(n+1) + ky)*(n+1) + kx.  Needs no GPU.
+ * (kz*(n+1) + ky)*(n+1) + kx.  EXX_KERNEL_PERIODIC (n even): 4 pi / |k|^2,
+ * k = 2 pi m / (n h), m in [0, n/2]^3, 0 at m = 0; (n/2+1)^3 doubles.
+ * Needs no GPU.
  */
 exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double omega, double* out_host);
 

@@ -31,9 +31,29 @@ namespace exx {
   X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(12) X(14) X(16) X(18) X(20) X(24) X(28)    \
   X(32) X(36) X(40) X(48) X(56) X(64) X(72) X(80) X(96) X(112) X(128) X(160)
 
+// periodic boundary conditions: half grids (grid = 2 N)
+#define EXX_PSIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96)
+
 #define EXX_DECL(N) const Ops* ops_f32_##N(); const Ops* ops_f64_##N();
 EXX_SIZES(EXX_DECL)
 #undef EXX_DECL
+#define EXX_DECL(N) const Ops* ops_pf32_##N(); const Ops* ops_pf64_##N();
+EXX_PSIZES(EXX_DECL)
+#undef EXX_DECL
+
+// periodic grid n = 2 N
+static const Ops* lookup_ops_periodic(int prec, int n) {
+  if (n % 2 != 0) return nullptr;
+  switch (n / 2) {
+#define EXX_CASE(N) \
+  case N:           \
+    return prec == EXX_FP64 ? ops_pf64_##N() : ops_pf32_##N();
+    EXX_PSIZES(EXX_CASE)
+#undef EXX_CASE
+    default:
+      return nullptr;
+  }
+}
 
 static const Ops* lookup_ops(int prec, int n) {
   switch (n) {
@@ -308,7 +328,8 @@ const char* exx_version(void) { return "exx-gb300 0.1 (sm_103a)"; }
 
 exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double omega, double* out_host) {
   if (n < 1 || !(h > 0.0) || out_host == nullptr) return EXX_ERR_INVALID_ARG;
-  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC)
+  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC &&
+      kernel != EXX_KERNEL_PERIODIC)
     return EXX_ERR_INVALID_ARG;
   return exx_host::kernel_spectrum_octant(n, h, kernel, omega, out_host) ? EXX_OK
                                                                           : EXX_ERR_INVALID_ARG;
@@ -349,7 +370,8 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   if (!(h[0] > 0.0) || !(h[1] > 0.0) || !(h[2] > 0.0) || !std::isfinite(alpha))
     return EXX_ERR_INVALID_ARG;
   if (precision != EXX_FP64 && precision != EXX_FP32) return EXX_ERR_INVALID_ARG;
-  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC)
+  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC &&
+      kernel != EXX_KERNEL_PERIODIC)
     return EXX_ERR_INVALID_ARG;
   if (flags & ~((unsigned)EXX_FLAG_VX_FP64 | EXX_FLAG_TILE(15))) return EXX_ERR_INVALID_ARG;
   const int tile_req = (int)((flags >> 8) & 15u);
@@ -359,9 +381,12 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   if (grid[0] != grid[1] || grid[0] != grid[2] || h[0] != h[1] || h[0] != h[2])
     return EXX_ERR_NOT_SUPPORTED;
   const int n = grid[0];
-  if (split_l1(2 * n) == 0) return EXX_ERR_NOT_SUPPORTED;
-  const Ops* ops = lookup_ops(precision, n);
+  const Ops* ops = kernel == EXX_KERNEL_PERIODIC ? lookup_ops_periodic(precision, n)
+                   : split_l1(2 * n) == 0       ? nullptr
+                                                : lookup_ops(precision, n);
   if (ops == nullptr || !ops->supported) return EXX_ERR_NOT_SUPPORTED;
+  // transforms of length 2 nh: nh = n (free BC, padded) or n / 2 (periodic)
+  const int nh = ops->n;
 
   exx_plan_t p = new exx_plan_s();
   p->n = n;
@@ -395,33 +420,37 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   }
   p->mine.assign(p->tiles.size(), 1);
 
-  // kernel spectrum (FP64, host), scaled by the inverse-FFT normalisation
-  const size_t m = (size_t)n + 1;
+  // kernel spectrum (FP64, host, one octant k <= nh), scaled by the
+  // inverse-FFT normalisation
+  const size_t m = (size_t)nh + 1;
   std::vector<double> Gh(m * m * m);
   if (!exx_host::kernel_spectrum_octant(n, p->h, kernel, p->omega, Gh.data())) {
     delete p;
     return EXX_ERR_INVALID_ARG;
   }
-  const double L = 2.0 * n;
+  const double L = 2.0 * nh;
   const double scale = 1.0 / (L * L * L);
   const size_t rs = precision == EXX_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * rs;
   // kernel table (scaled by 1/(2n)^3; for FP32 with the forward transforms'
   // gains divided out) and twiddle tables (exx_ops.cuh)
-  std::vector<unsigned char> gbuf(exx::kernel_table_bytes(n, rs, ops->table_fold_y)), twbuf(exx::twiddle_count(n) * cs);
+  std::vector<unsigned char> gbuf(exx::kernel_table_bytes(nh, rs, ops->table_fold_y)),
+      twbuf(exx::twiddle_count(nh) * cs);
   std::vector<double> gx, gz;
   if (ops->gains) {
     gx.resize(m);
-    gz.resize(2 * (size_t)n);
+    gz.resize(2 * (size_t)nh);
     ops->gains(gx.data(), gz.data());
   }
   if (precision == EXX_FP64) {
-    exx::build_kernel_table<double>(n, ops->table_fold_y, Gh.data(), scale, nullptr, nullptr, gbuf.data());
-    exx::build_twiddles(n, reinterpret_cast<double*>(twbuf.data()));
+    exx::build_kernel_table<double>(nh, ops->table_fold_y, Gh.data(), scale, nullptr, nullptr,
+                                    gbuf.data());
+    exx::build_twiddles(nh, reinterpret_cast<double*>(twbuf.data()));
   } else {
-    exx::build_kernel_table<float>(n, ops->table_fold_y, Gh.data(), scale, gx.empty() ? nullptr : gx.data(),
-                                   gz.empty() ? nullptr : gz.data(), gbuf.data());
-    exx::build_twiddles(n, reinterpret_cast<float*>(twbuf.data()));
+    exx::build_kernel_table<float>(nh, ops->table_fold_y, Gh.data(), scale,
+                                   gx.empty() ? nullptr : gx.data(), gz.empty() ? nullptr : gz.data(),
+                                   gbuf.data());
+    exx::build_twiddles(nh, reinterpret_cast<float*>(twbuf.data()));
   }
 
   const long long n3 = (long long)n * n * n;
@@ -439,7 +468,7 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   EXX_ALLOC(p->d_pairs, pairs.size() * sizeof(int4));
   EXX_ALLOC(p->epart, (size_t)p->maxpairs * nper * sizeof(double));
   EXX_ALLOC(p->Epair, (size_t)p->P * sizeof(double));
-  EXX_ALLOC(p->X2, (size_t)p->maxpairs * m * n * (2 * n) * cs);
+  EXX_ALLOC(p->X2, (size_t)p->maxpairs * m * n * (2 * nh) * cs);
   EXX_ALLOC(p->V, (size_t)p->maxpairs * n3 * rs);
   if (precision == EXX_FP32 && !(flags & EXX_FLAG_VX_FP64)) {
     EXX_ALLOC(p->vacc, (size_t)norb * n3 * sizeof(double));
@@ -493,7 +522,7 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
   const int n = p->n, N = p->N;
   const long long n3 = (long long)n * n * n;
   const double h3 = p->h * p->h * p->h;
-  const int nper = (n + 1) * p->ops->nyb;
+  const int nper = (p->ops->n + 1) * p->ops->nyb;
   const size_t rs = p->prec == EXX_FP64 ? sizeof(double) : sizeof(float);
   double* acc = nullptr;
   if (apply) {

@@ -42,12 +42,16 @@ struct F32c2 {
 template <> struct cvec<F32c> { using type = F32c2; };
 template <> struct creal<F32c2> { using type = F32c; };
 
-template <int N> struct GainModel {
+// PER: periodic boundary conditions (full lines of 2N points, nothing pruned);
+// otherwise free (lines of N points padded to 2N).
+template <int N, bool PER = false> struct GainModel {
   using R = F32c;
   using C = F32c2;
   static constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   static constexpr int X1 = split_x(N), X2 = N / X1;
-  static constexpr bool PX = (N % 2) == 0;
+  static constexpr int G = PER ? L : N;  // input samples per line
+  static constexpr int NIN = PER ? L1 : H1;
+  static constexpr bool PX = !PER && (N % 2) == 0;
   static constexpr int XIN = PX ? X1 / 2 : X1;
 
   // table entry w^e = exp(-2 pi i e / L), rounded as build_twiddles rounds it
@@ -57,13 +61,13 @@ template <int N> struct GainModel {
   }
   static C raw(double a, double b) { return mkc<C>(R(a, R::Raw{}), R(b, R::Raw{})); }
 
-  // pruned forward line transform of the y and z passes: in[n], n < N -> out[k]
+  // forward line transform of the y and z passes: in[n], n < G -> out[k]
   static void line(const C* in, C* out) {
     C B[L];  // [n2][k1]
     for (int n2 = 0; n2 < L2; ++n2) {
       C v[L1];
-      for (int n1 = 0; n1 < H1; ++n1) v[n1] = in[L2 * n1 + n2];
-      dft_halfin<L1, -1>(v);
+      for (int n1 = 0; n1 < NIN; ++n1) v[n1] = in[L2 * n1 + n2];
+      dft_fwd_in<L1, PER>(v);
       B[n2 * L1] = v[0];
       for (int k1 = 1; k1 < L1; ++k1) B[n2 * L1 + k1] = cmul(v[k1], tw((long)n2 * k1));
     }
@@ -75,7 +79,7 @@ template <int N> struct GainModel {
     }
   }
 
-  // forward x pass: real in[m], m < N -> half spectrum out[k], k = 0..N
+  // forward x pass: real in[m], m < G -> half spectrum out[k], k = 0..N
   static void xline(const double* in, C* out) {
     C Z1[N], Z[N];
     for (int n2 = 0; n2 < X2; ++n2) {
@@ -83,7 +87,7 @@ template <int N> struct GainModel {
       for (int n1 = 0; n1 < X1; ++n1) v[n1] = raw(0.0, 0.0);
       for (int n1 = 0; n1 < XIN; ++n1) {
         const int m = X2 * n1 + n2;
-        v[n1] = raw(2 * m < N ? in[2 * m] : 0.0, 2 * m + 1 < N ? in[2 * m + 1] : 0.0);
+        v[n1] = raw(2 * m < G ? in[2 * m] : 0.0, 2 * m + 1 < G ? in[2 * m + 1] : 0.0);
       }
       if constexpr (PX) dft_halfin<X1, -1>(v);
       else dft<X1, 1, -1>(v);
@@ -107,10 +111,10 @@ template <int N> struct GainModel {
   // |d|^2 per output: gx[k], k = 0..N (x pass); gz[k], k < L (y and z passes)
   static void gains(double* gx, double* gz) {
     std::vector<std::complex<double>> az(L), ax(N + 1);
-    std::vector<C> in(N), out(L), xo(N + 1);
-    std::vector<double> rin(N);
-    for (int n = 0; n < N; ++n) {
-      for (int j = 0; j < N; ++j) {
+    std::vector<C> in(G), out(L), xo(N + 1);
+    std::vector<double> rin(G);
+    for (int n = 0; n < G; ++n) {
+      for (int j = 0; j < G; ++j) {
         in[j] = raw(j == n ? 1.0 : 0.0, 0.0);
         rin[j] = j == n ? 1.0 : 0.0;
       }
@@ -125,8 +129,8 @@ template <int N> struct GainModel {
                    std::complex<double>(xo[k].x.v, xo[k].y.v);
       }
     }
-    for (int k = 0; k < L; ++k) gz[k] = std::norm(az[k] / (double)N);
-    for (int k = 0; k <= N; ++k) gx[k] = std::norm(ax[k] / (double)N);
+    for (int k = 0; k < L; ++k) gz[k] = std::norm(az[k] / (double)G);
+    for (int k = 0; k <= N; ++k) gx[k] = std::norm(ax[k] / (double)G);
   }
 };
 

@@ -60,6 +60,18 @@ template <int L1, int L2> struct Scr {
 
 template <typename R> __device__ __forceinline__ R sq(R a) { return a * a; }
 
+// Line transforms of the two boundary conditions: free (zero-padded line of
+// length 2n, second half of the input zero, second half of the inverse output
+// unneeded: pruned) or periodic (full line, nothing pruned).
+template <int P, bool FULL, typename C> EXX_HD void dft_fwd_in(C* v) {
+  if constexpr (FULL) dft<P, 1, -1>(v);
+  else dft_halfin<P, -1>(v);
+}
+template <int P, bool FULL, typename C> EXX_HD void dft_inv_out(C* v) {
+  if constexpr (FULL) dft<P, 1, 1>(v);
+  else dft_halfout<P, 1>(v);
+}
+
 // 16-byte asynchronous global -> shared copy (cp.async); src_bytes = 0 fills
 // the destination with zeros without reading.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
@@ -108,7 +120,9 @@ template <typename C> EXX_HD void split_step(C zk, C zm, C w, C& xk, C& xm) {
 // the columns y in [c n/2, (c+1) n/2) of every row; the x passes stay local,
 // the y passes of a CTA's rows read the other half of each row from the peer's
 // shared memory (distributed shared memory).
-template <typename R, int N, int NT, int MINB, int Q, int CL>
+// PER: periodic boundary conditions: the grid has G = 2n points per axis, the
+// lines are not padded and nothing is pruned (N is then half the grid).
+template <typename R, int N, int NT, int MINB, int Q, int CL, bool PER>
 __global__ void __launch_bounds__(NT, MINB)
 k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
          const int4* __restrict__ pairs, cplx<R>* __restrict__ X, const cplx<R>* __restrict__ tw_g,
@@ -116,11 +130,13 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int X1 = split_x(N), X2 = N / X1;
-  constexpr bool PX = (N % 2) == 0;  // pruned x input
+  constexpr int G = PER ? 2 * N : N;  // grid points per axis
+  constexpr bool PX = !PER && (N % 2) == 0;  // pruned x input
   constexpr int XIN = PX ? X1 / 2 : X1;
-  constexpr int NY = N / CL, SP = NY + 1;
-  constexpr int NB = CL == 1 ? H1 : NY / L2;  // y = L2 n1 + n2 lies in half n1 / NB
-  static_assert(CL == 1 || (Q == 0 && N % 2 == 0 && NY % L2 == 0), "cluster split");
+  constexpr int NIN = PER ? L1 : H1;  // nonzero inputs of the y pass-1 DFTs
+  constexpr int NY = G / CL, SP = NY + 1;
+  constexpr int NB = CL == 1 ? L1 : NY / L2;  // y = L2 n1 + n2 lies in half n1 / NB
+  static_assert(CL == 1 || (Q == 0 && G % 2 == 0 && NY % L2 == 0), "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // twiddle tables (packed layout of build_twiddles): TY[k1][n2] = w^(n2 k1)
   // for the y pass and TX[k1][n2] = w^(2 n2 k1) for the x pass, so that
@@ -135,8 +151,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   const int p = blockIdx.y;
   const int4 pr = pairs[p];  // (i, j, pair id, molecule slot)
   const R* psi = psi_tab ? psi_tab[pr.w] : psi0;
-  const R* __restrict__ pi = psi + (long long)pr.x * n3 + (long long)z * N * N;
-  const R* __restrict__ pj = psi + (long long)pr.y * n3 + (long long)z * N * N;
+  const R* __restrict__ pi = psi + (long long)pr.x * n3 + (long long)z * G * G;
+  const R* __restrict__ pj = psi + (long long)pr.y * n3 + (long long)z * G * G;
   for (int t = tid; t < L + N; t += NT) ty[t] = tw_g[L + t];
   __syncthreads();
 
@@ -144,14 +160,14 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   // column y - y0
   for (int u = tid; u < NY * X2; u += NT) {
     const int yl = u / X2, n2 = u - yl * X2;
-    const R* ri = pi + (y0 + yl) * N;
-    const R* rj = pj + (y0 + yl) * N;
+    const R* ri = pi + (y0 + yl) * G;
+    const R* rj = pj + (y0 + yl) * G;
     C v[X1];
 #pragma unroll
     for (int n1 = 0; n1 < XIN; ++n1) {
       const int m = X2 * n1 + n2;
-      const R a = (2 * m < N) ? ri[2 * m] * rj[2 * m] : R(0);
-      const R b = (2 * m + 1 < N) ? ri[2 * m + 1] * rj[2 * m + 1] : R(0);
+      const R a = (2 * m < G) ? ri[2 * m] * rj[2 * m] : R(0);
+      const R b = (2 * m + 1 < G) ? ri[2 * m + 1] * rj[2 * m + 1] : R(0);
       v[n1] = mkc<C>(a, b);
     }
     if constexpr (PX) {
@@ -231,8 +247,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
           const int rb = srow<SP, X1>(kx);
           C v[L1];
 #pragma unroll
-          for (int n1 = 0; n1 < H1; ++n1) v[n1] = (n1 < NB ? h0 : h1)[rb + L2 * (n1 % NB) + n2];
-          dft_halfin<L1, -1>(v);
+          for (int n1 = 0; n1 < NIN; ++n1) v[n1] = (n1 < NB ? h0 : h1)[rb + L2 * (n1 % NB) + n2];
+          dft_fwd_in<L1, PER>(v);
           C* o = Sw + n2 * Scr<L1, L2>::row;
           o[0] = v[0];
 #pragma unroll
@@ -246,7 +262,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 #pragma unroll
         for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
         dft<L2, 1, -1>(v);
-        C* out = X + (((long long)p * (N + 1) + kx) * N + z) * L + cl16;
+        C* out = X + (((long long)p * (N + 1) + kx) * G + z) * L + cl16;
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
       }
@@ -265,8 +281,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
         const C* row = Sl + srow<SP, X1>(r0 + r);
         C v[L1];
 #pragma unroll
-        for (int n1 = 0; n1 < H1; ++n1) v[n1] = row[L2 * n1 + n2];
-        dft_halfin<L1, -1>(v);
+        for (int n1 = 0; n1 < NIN; ++n1) v[n1] = row[L2 * n1 + n2];
+        dft_fwd_in<L1, PER>(v);
         C* o = S + r * Scr<L1, L2>::line + n2 * Scr<L1, L2>::row;
         o[0] = v[0];
 #pragma unroll
@@ -280,7 +296,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 #pragma unroll
         for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
         dft<L2, 1, -1>(v);
-        C* out = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
+        C* out = X + (((long long)p * (N + 1) + (r0 + r)) * G + z) * L + k1;
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
       }
@@ -299,7 +315,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 // asynchronous 16-byte copies that overlap the first pass (FP32 rows aligned
 // to 16 bytes, and only where it costs no occupancy); otherwise the values
 // are read from global memory in the second pass.
-template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool ENERGY_ONLY>
+template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool PER, bool ENERGY_ONLY>
 __global__ void __launch_bounds__(32 * NW, MINB)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
         double* __restrict__ epart) {
@@ -339,16 +355,18 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
     }
     cp_async_commit();
   }
-  C* col = X + (((long long)p * M + kx) * N) * L + (valid ? ky : 0);
+  constexpr int G = PER ? 2 * N : N;  // z planes stored (grid points per axis)
+  constexpr int NIN = PER ? L1 : H1;   // nonzero inputs / kept outputs per DFT_L1
+  C* col = X + (((long long)p * M + kx) * G) * L + (valid ? ky : 0);
   __syncthreads();
 
   // forward, pass 1
   for (int n2 = warp; n2 < L2; n2 += NW) {
     C v[L1];
 #pragma unroll
-    for (int n1 = 0; n1 < H1; ++n1)
+    for (int n1 = 0; n1 < NIN; ++n1)
       v[n1] = valid ? col[(long long)(L2 * n1 + n2) * L] : mkc<C>(R(0), R(0));
-    dft_halfin<L1, -1>(v);
+    dft_fwd_in<L1, PER>(v);
     if (lane < W) {
       buf[(n2 * L1) * W + lane] = v[0];
 #pragma unroll
@@ -395,10 +413,10 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 #pragma unroll
       for (int k1 = 0; k1 < L1; ++k1)
         v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
-      dft_halfout<L1, 1>(v);
+      dft_inv_out<L1, PER>(v);
       if (valid) {
 #pragma unroll
-        for (int m1 = 0; m1 < H1; ++m1) col[(long long)(L2 * m1 + m2) * L] = v[m1];
+        for (int m1 = 0; m1 < NIN; ++m1) col[(long long)(L2 * m1 + m2) * L] = v[m1];
       }
     }
   }
@@ -426,17 +444,20 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 // samples of the real line: V[2m] = Re, V[2m+1] = Im, kept for x < n.
 // CL = 2: two-CTA cluster as in fwd_xy; a CTA's y passes write the other half
 // of each row into the peer's slab, then each CTA transforms its own columns.
-template <typename R, int N, int NT, int MINB, int Q, int CL>
+// PER: periodic boundary conditions (see fwd_xy).
+template <typename R, int N, int NT, int MINB, int Q, int CL, bool PER>
 __global__ void __launch_bounds__(NT, MINB)
 k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __restrict__ tw_g) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int X1 = split_x(N), X2 = N / X1;
-  constexpr bool PX = (N % 2) == 0;
+  constexpr int G = PER ? 2 * N : N;  // grid points per axis
+  constexpr bool PX = !PER && (N % 2) == 0;
   constexpr int XOUT = PX ? X1 / 2 : X1;
-  constexpr int NY = N / CL, SP = NY + 1;
-  constexpr int NB = CL == 1 ? H1 : NY / L2;  // y = L2 m1 + m2 lies in half m1 / NB
-  static_assert(CL == 1 || (Q == 0 && N % 2 == 0 && NY % L2 == 0), "cluster split");
+  constexpr int NOUT = PER ? L1 : H1;  // kept outputs of the y pass-2 DFTs
+  constexpr int NY = G / CL, SP = NY + 1;
+  constexpr int NB = CL == 1 ? L1 : NY / L2;  // y = L2 m1 + m2 lies in half m1 / NB
+  static_assert(CL == 1 || (Q == 0 && G % 2 == 0 && NY % L2 == 0), "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);  // w^k, high parts [L]
   C* ti = tw + L;                          // TI[m2][k1] = w^(m2 k1) [L] (see fwd_xy)
@@ -473,7 +494,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
       const int kx = r0 + hr;
       const bool rv = kx <= N;
       if (rv && cl16 < L1) {
-        const C* in = X + (((long long)p * (N + 1) + kx) * N + z) * L + cl16;
+        const C* in = X + (((long long)p * (N + 1) + kx) * G + z) * L + cl16;
         C v[L2];
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
@@ -490,10 +511,10 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
           C v[L1];
 #pragma unroll
           for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
-          dft_halfout<L1, 1>(v);
+          dft_inv_out<L1, PER>(v);
           const int rb = srow<SP, X1>(kx);
 #pragma unroll
-          for (int m1 = 0; m1 < H1; ++m1) (m1 < NB ? h0 : h1)[rb + L2 * (m1 % NB) + m2] = v[m1];
+          for (int m1 = 0; m1 < NOUT; ++m1) (m1 < NB ? h0 : h1)[rb + L2 * (m1 % NB) + m2] = v[m1];
         }
       }
       __syncwarp();
@@ -505,7 +526,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
       const int nr = min(Q, N + 1 - r0);
       for (int u = tid; u < nr * L1; u += NT) {
         const int r = u / L1, k1 = u - r * L1;
-        const C* in = X + (((long long)p * (N + 1) + (r0 + r)) * N + z) * L + k1;
+        const C* in = X + (((long long)p * (N + 1) + (r0 + r)) * G + z) * L + k1;
         C v[L2];
 #pragma unroll
         for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
@@ -522,10 +543,10 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
         C v[L1];
 #pragma unroll
         for (int k1 = 0; k1 < L1; ++k1) v[k1] = q[k1];
-        dft_halfout<L1, 1>(v);
+        dft_inv_out<L1, PER>(v);
         C* row = Sl + srow<SP, X1>(r0 + r);
 #pragma unroll
-        for (int m1 = 0; m1 < H1; ++m1) row[L2 * m1 + m2] = v[m1];
+        for (int m1 = 0; m1 < NOUT; ++m1) row[L2 * m1 + m2] = v[m1];
       }
       __syncthreads();
     }
@@ -565,7 +586,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   }
   __syncthreads();
   // x inverse, pass 2: units (y, m2), m2 fastest (coalesced writes of row y)
-  R* Vz = V + ((long long)p * N + z) * N * N;
+  R* Vz = V + ((long long)p * G + z) * G * G;
   for (int u = tid; u < NY * X2; u += NT) {
     const int y = u / X2, m2 = u - y * X2;
     C v[X1];
@@ -573,12 +594,12 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
     for (int k1 = 0; k1 < X1; ++k1) v[k1] = Sl[srow<SP, X1>(m2 * X1 + k1) + y];
     if constexpr (PX) dft_halfout<X1, 1>(v);
     else dft<X1, 1, 1>(v);
-    R* row = Vz + (long long)(y0 + y) * N;
+    R* row = Vz + (long long)(y0 + y) * G;
 #pragma unroll
     for (int m1 = 0; m1 < XOUT; ++m1) {
       const int m = X2 * m1 + m2;
-      if (2 * m < N) row[2 * m] = v[m1].x;
-      if (2 * m + 1 < N) row[2 * m + 1] = v[m1].y;
+      if (2 * m < G) row[2 * m] = v[m1].x;
+      if (2 * m + 1 < G) row[2 * m + 1] = v[m1].y;
     }
   }
 }

@@ -12,7 +12,9 @@
 namespace exx {
 
 struct Ops {
-  int n = 0;
+  int n = 0;         // half the line length of the transforms (line 2n)
+  int grid = 0;      // grid points per axis: n (free BC) or 2n (periodic)
+  bool periodic = false;
   bool supported = false;
   int nyb = 0;             // zconv column blocks per kx plane
   int nt_a = 0, nt_c = 0;  // threads per CTA of fwd_xy / inv_yx
@@ -154,17 +156,18 @@ void build_kernel_table(int n, bool fold_y, const double* octant, double scale, 
   }
 }
 
-template <typename R, int N> struct OpsImpl {
+template <typename R, int N, bool PER = false> struct OpsImpl {
   using C = cplx<R>;
+  static constexpr int G = PER ? 2 * N : N;  // grid points per axis
   static constexpr int L = 2 * N;
   static constexpr int L1 = split_l1(L);
   static constexpr int L2 = L1 ? L / L1 : 1;
   static constexpr int X1 = split_x(N);
-  static constexpr size_t slab = X1 ? (size_t)slab_elems(N, N) * sizeof(C) : 0;
+  static constexpr size_t slab = X1 ? (size_t)slab_elems(N, G) * sizeof(C) : 0;
   // two-CTA split: half the columns per CTA (the y-pass index split must fall
   // on a whole number of length-L2 groups)
-  static constexpr bool split_ok = X1 && L1 && N % 2 == 0 && (N / 2) % L2 == 0;
-  static constexpr size_t slab2 = split_ok ? (size_t)slab_elems(N, N / 2) * sizeof(C) : 0;
+  static constexpr bool split_ok = X1 && L1 && G % 2 == 0 && (G / 2) % L2 == 0;
+  static constexpr size_t slab2 = split_ok ? (size_t)slab_elems(N, G / 2) * sizeof(C) : 0;
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
   static constexpr SlabShape SA = slab_shape(slab + (size_t)(L + N) * sizeof(C),
                                              slab2 + (size_t)(L + N) * sizeof(C), split_ok, line, true);
@@ -194,16 +197,16 @@ template <typename R, int N> struct OpsImpl {
   static cudaError_t setup() {
     if constexpr (ok) {
       cudaError_t e;
-      e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A>,
+      e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A, PER>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, false>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, true>,
+      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC, CL_C>,
+      return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC, CL_C, PER>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
     }
     return cudaErrorNotSupported;
@@ -211,7 +214,7 @@ template <typename R, int N> struct OpsImpl {
   static void fwd_xy(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
                      void* X, const void* tw, long long n3, cudaStream_t st) {
     if constexpr (ok)
-      launch_slab<CL_A>(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A>, dim3(N * CL_A, npair), NT_A,
+      launch_slab<CL_A>(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A, PER>, dim3(G * CL_A, npair), NT_A,
                         smem_a, st, static_cast<const R*>(psi),
                         reinterpret_cast<const R* const*>(psi_tab), pairs, static_cast<C*>(X),
                         static_cast<const C*>(tw), n3);
@@ -221,22 +224,24 @@ template <typename R, int N> struct OpsImpl {
     if constexpr (ok) {
       const dim3 grid(NYB, N + 1, npair);
       if (energy_only)
-        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, true><<<grid, 32 * NW, smem_b, st>>>(
+        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, true><<<grid, 32 * NW, smem_b, st>>>(
             static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
       else
-        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, false><<<grid, 32 * NW, smem_b, st>>>(
+        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, false><<<grid, 32 * NW, smem_b, st>>>(
             static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
     }
   }
   static void inv_yx(const void* X, void* V, const void* tw, int npair, cudaStream_t st) {
     if constexpr (ok)
-      launch_slab<CL_C>(k_inv_yx<R, N, NT_C, MINB_C, QC, CL_C>, dim3(N * CL_C, npair), NT_C,
+      launch_slab<CL_C>(k_inv_yx<R, N, NT_C, MINB_C, QC, CL_C, PER>, dim3(G * CL_C, npair), NT_C,
                         smem_c, st, static_cast<const C*>(X), static_cast<R*>(V),
                         static_cast<const C*>(tw));
   }
   static Ops make() {
     Ops o;
     o.n = N;
+    o.grid = G;
+    o.periodic = PER;
     o.supported = ok;
     o.nyb = NYB;
     o.nt_a = NT_A;
@@ -247,7 +252,7 @@ template <typename R, int N> struct OpsImpl {
     o.smem_c = smem_c;
     o.setup = &setup;
     o.table_fold_y = fold_y;
-    if constexpr (ok && sizeof(R) == 4) o.gains = &GainModel<N>::gains;
+    if constexpr (ok && sizeof(R) == 4) o.gains = &GainModel<N, PER>::gains;
     o.fwd_xy = &fwd_xy;
     o.zconv = &zconv;
     o.inv_yx = &inv_yx;
@@ -256,6 +261,19 @@ template <typename R, int N> struct OpsImpl {
 };
 
 }  // namespace exx
+
+// periodic boundary conditions on a grid of 2N points per axis
+#define EXX_DEFINE_OPS_PER(N)                                       \
+  namespace exx {                                                   \
+  const Ops* ops_pf32_##N() {                                       \
+    static const Ops o = OpsImpl<float, N, true>::make();           \
+    return &o;                                                      \
+  }                                                                 \
+  const Ops* ops_pf64_##N() {                                       \
+    static const Ops o = OpsImpl<double, N, true>::make();          \
+    return &o;                                                      \
+  }                                                                 \
+  }
 
 #define EXX_DEFINE_OPS(N)                                           \
   namespace exx {                                                   \

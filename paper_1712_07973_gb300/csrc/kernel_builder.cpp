@@ -203,12 +203,31 @@ void hockney_spectrum(int n, double h, double* out) {
   for (size_t i = 0; i < G.size(); ++i) out[i] = G[i];
 }
 
+// Periodic cell of n points per axis (n even): 4 pi / |k|^2 with
+// k = 2 pi m / (n h), m in [0, n/2]^3 (the signed frequencies fold onto this
+// octant), the k = 0 term removed.  out: (n/2+1)^3 doubles.
+void periodic_spectrum(int n, double h, double* out) {
+  const int m = n / 2 + 1;
+  const double c = 2.0 * kPi / (n * h);
+  for (int kz = 0; kz < m; ++kz)
+    for (int ky = 0; ky < m; ++ky)
+      for (int kx = 0; kx < m; ++kx) {
+        const double k2 = c * c * ((double)kx * kx + (double)ky * ky + (double)kz * kz);
+        out[((size_t)kz * m + ky) * m + kx] = k2 > 0.0 ? 4.0 * kPi / k2 : 0.0;
+      }
+}
+
 }  // namespace
 
 // kind: 0 = band-limited (sinc), 1 = Hockney, 2 = band-limited erfc(omega r)/r
-// (omega > 0).  out: (n+1)^3 doubles.
+// (omega > 0): out (n+1)^3 doubles; 3 = periodic (n even): out (n/2+1)^3.
 bool kernel_spectrum_octant(int n, double h, int kind, double omega, double* out) {
   if (n < 1 || !(h > 0.0) || out == nullptr) return false;
+  if (kind == 3) {
+    if (n % 2 != 0) return false;
+    periodic_spectrum(n, h, out);
+    return true;
+  }
   if (kind == 0) sinc_spectrum(n, h, 0.0, out);
   else if (kind == 1) hockney_spectrum(n, h, out);
   else if (kind == 2 && omega > 0.0 && std::isfinite(omega)) sinc_spectrum(n, h, omega * h, out);

@@ -14,10 +14,11 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["ExxError", "ExxPlan", "ExxBatch", "load_library", "kernel_spectrum", "shard_tiles", "EXPORTS",
-           "FP64", "FP32", "KERNEL_SINC", "KERNEL_HOCKNEY", "FLAG_VX_FP64"]
+           "FP64", "FP32", "KERNEL_SINC", "KERNEL_HOCKNEY", "KERNEL_ERFC", "KERNEL_PERIODIC",
+           "FLAG_VX_FP64"]
 
 FP64, FP32 = 0, 1
-KERNEL_SINC, KERNEL_HOCKNEY, KERNEL_ERFC = 0, 1, 2
+KERNEL_SINC, KERNEL_HOCKNEY, KERNEL_ERFC, KERNEL_PERIODIC = 0, 1, 2, 3
 FLAG_VX_FP64 = 1
 STATUS = ["EXX_OK", "EXX_ERR_INVALID_ARG", "EXX_ERR_CUDA", "EXX_ERR_OOM", "EXX_ERR_TIMEOUT",
           "EXX_ERR_NOT_SUPPORTED"]
@@ -111,11 +112,13 @@ def _check(status, where, plan=None):
 
 
 def kernel_spectrum(n, h, kind=KERNEL_SINC, omega=0.0):
-    """Host-only FP64 octant of the padded kernel spectrum, shape (n+1,)*3."""
-    out = np.zeros((n + 1) ** 3, dtype=np.float64)
+    """Host-only FP64 octant of the kernel spectrum: (n+1,)*3 for the padded
+    free-boundary kernels, (n/2+1,)*3 for KERNEL_PERIODIC."""
+    m = n // 2 + 1 if kind == KERNEL_PERIODIC else n + 1
+    out = np.zeros(m ** 3, dtype=np.float64)
     _check(load_library().exx_kernel_spectrum(n, float(h), int(kind), float(omega),
                                               out.ctypes.data_as(_c_double_p)), "exx_kernel_spectrum")
-    return out.reshape(n + 1, n + 1, n + 1)
+    return out.reshape(m, m, m)
 
 
 def shard_tiles(norb, tile=0, nranks=1):
@@ -175,7 +178,8 @@ class ExxPlan:
         self.occ = occ
         self.norb = int(occ.size)
         self.precision = {"fp64": FP64, "fp32": FP32}[precision]
-        self.kernel = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY, "erfc": KERNEL_ERFC}[kernel]
+        self.kernel = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY, "erfc": KERNEL_ERFC,
+                       "periodic": KERNEL_PERIODIC}[kernel]
         self.omega = float(omega)
         self.vx_fp64 = bool(vx_fp64)
         self.dtype = torch.float64 if self.precision == FP64 else torch.float32

@@ -98,7 +98,7 @@ def test_kernel_spectrum_rejects_bad_arguments(lib):
     p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     assert lib.exx_kernel_spectrum(0, 0.4, 0, 0.0, p) == 1
     assert lib.exx_kernel_spectrum(1, -1.0, 0, 0.0, p) == 1
-    assert lib.exx_kernel_spectrum(1, 0.4, 3, 0.0, p) == 1
+    assert lib.exx_kernel_spectrum(1, 0.4, 4, 0.0, p) == 1
     assert lib.exx_kernel_spectrum(1, 0.4, 0, 0.0, None) == 1
     assert lib.exx_kernel_spectrum(1, 0.4, 2, 0.0, p) == 1   # erfc needs omega > 0
     assert lib.exx_kernel_spectrum(1, 0.4, 2, -0.1, p) == 1
@@ -118,3 +118,19 @@ def test_host_erfc_spectrum_matches_oracle(lib, n, h, w):
 def test_erfc_plan_needs_omega(lib):
     # the plain constructor refuses the screened kernel (no omega to pass)
     assert _create(lib, kernel=2)[0] == 1
+
+
+@pytest.mark.parametrize("n,h", [(8, 0.5), (12, 0.4), (32, 0.3)])
+def test_host_periodic_spectrum_matches_oracle(lib, n, h):
+    from paper_1712_07973_gb300 import exx
+    got = exx.kernel_spectrum(n, h, exx.KERNEL_PERIODIC)  # [kz][ky][kx], k <= n/2
+    ref = o.kernel_spectrum_periodic(n, h)                # rfftn layout (n, n, n/2+1)
+    m = n // 2 + 1
+    assert np.allclose(got, ref[:m, :m, :m], rtol=1e-14, atol=0)
+
+
+def test_periodic_needs_even_supported_grid(lib):
+    assert _create(lib, grid=(9, 9, 9), kernel=3)[0] == 5     # odd
+    assert _create(lib, grid=(10, 10, 10), kernel=3)[0] == 5   # 10 not compiled
+    out = np.zeros(8)
+    assert lib.exx_kernel_spectrum(3, 0.4, 3, 0.0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1

@@ -52,7 +52,10 @@ def _gpu(torch_dev, psi, occ, alpha, h, precision, kernel="sinc", vx_fp64=False,
 
 def _oracle(psi, occ, alpha, h, kernel=o.KERNEL_SINC, omega=0.0):
     n = psi.shape[1]
-    Gh = o.kernel_spectrum(o.kernel_real_space(n, h, kernel, omega=omega))
+    if kernel == "periodic":
+        Gh = o.kernel_spectrum_periodic(n, h)
+    else:
+        Gh = o.kernel_spectrum(o.kernel_real_space(n, h, kernel, omega=omega))
     Ex, vx, Eij = o.exx(psi, occ, alpha, h, Gh)
     return Ex, vx, Eij[np.triu_indices(psi.shape[0])]
 
@@ -320,3 +323,37 @@ def test_spin_polarised_channels(torch_dev):
     assert Es == pytest.approx(0.5 * E0, rel=1e-13)
     sp.close()
     sp2.close()
+
+
+# ------------------------------------------------ periodic boundary conditions
+
+@pytest.mark.parametrize("n", [8, 12, 16, 24, 32, 48])
+def test_periodic_fp64(torch_dev, n):
+    # no padding, full-length transforms, 4 pi/k^2 with k = 0 removed
+    psi = _orbitals(n, 3, seed=70 + n, h=0.5)
+    occ = np.array([2.0, 1.5, 2.0])
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.5, "fp64", kernel="periodic"),
+                 _oracle(psi, occ, 0.25, 0.5, "periodic"))
+
+
+@pytest.mark.parametrize("n,prec", [(64, "fp32"), (96, "fp32"), (128, "fp64")])
+def test_periodic_larger_grids(torch_dev, n, prec):
+    psi = _orbitals(n, 3, seed=90 + n, h=0.4)
+    occ = np.full(3, 2.0)
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, 0.25, 0.4, prec, kernel="periodic")
+    Eo, vxo, Eijo = _oracle(psi, occ, 0.25, 0.4, "periodic")
+    tol = 1e-10 * abs(Eo) if prec == "fp64" else 1e-6
+    assert abs(E - Eo) <= tol and abs(Ee - Eo) <= tol, (E, Ee, Eo)
+    vt = 1e-10 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(vx - vxo)) <= vt * np.max(np.abs(vxo))
+
+
+def test_periodic_fp32_192(torch_dev):
+    # the largest compiled periodic grid (one 640-thread CTA per slab)
+    psi = _orbitals(192, 2, seed=7, h=0.35)
+    occ = np.full(2, 2.0)
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, 0.25, 0.35, "fp32", kernel="periodic")
+    Eo, vxo, Eijo = _oracle(psi, occ, 0.25, 0.35, "periodic")
+    assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6, (E, Ee, Eo)
+    assert np.max(np.abs(Eij - Eijo)) <= 1e-6
+    assert np.max(np.abs(vx - vxo)) <= 2e-6 * np.max(np.abs(vxo))
