@@ -51,6 +51,8 @@ def args_parse():
                     help="orbital workload of the timed step (default: 64 orbitals on 96^3)")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 16-molecule batched workload (one graph launch)")
+    ap.add_argument("--bc", choices=["free", "periodic"], default="free",
+                    help="boundary conditions: free (zero-padded 2n FFTs) or periodic cell")
     ap.add_argument("--norb", type=int, default=0,
                     help="use only the first NORB orbitals (small profiling cases)")
     return ap.parse_args()
@@ -146,23 +148,25 @@ def tile_list(N, T):
     return out
 
 
-def algorithmic_bytes(n, N, T, rs=4):
+def algorithmic_bytes(n, N, T, rs=4, periodic=False):
     """Minimal HBM bytes of each kernel kind over one exx_apply.
 
-    Per pair: fwd_xy writes the y-transformed spectrum X2 ((n+1) n 2n complex);
+    Transforms of length 2h, h = n (free BC, padded) or n/2 (periodic).  Per
+    pair: fwd_xy writes the y-transformed spectrum X2 ((h+1) n 2h complex);
     zconv reads it and writes X3 in place; inv_yx reads X3 and writes V (n^3);
     accum reads V.  Per tile: fwd_xy and accum read the tile's orbitals once,
     accum reads and writes their FP64 accumulators once; zconv reads the
-    kernel octant ((n+1)^3) once per launch.
+    kernel table ((h+1) (2h)^2) once per launch.
     """
     cs = 2 * rs
-    spec = (n + 1) * n * 2 * n * cs
+    hl = n // 2 if periodic else n
+    spec = (hl + 1) * n * 2 * hl * cs
     n3 = n ** 3
     tot = {"fwd_xy": 0, "zconv": 0, "inv_yx": 0, "accum": 0}
     for npair, ti, tj, diag in tile_list(N, T):
         orbs = ti if diag else ti + tj
         tot["fwd_xy"] += orbs * n3 * rs + npair * spec
-        tot["zconv"] += 2 * npair * spec + (n + 1) * (2 * n) ** 2 * rs
+        tot["zconv"] += 2 * npair * spec + (hl + 1) * (2 * hl) ** 2 * rs
         tot["inv_yx"] += npair * spec + npair * n3 * rs
         tot["accum"] += npair * n3 * rs + orbs * n3 * rs + 2 * orbs * n3 * 8
     return tot
@@ -183,12 +187,13 @@ def committed_traffic(kernel):
 
 
 # ------------------------------------------------------------ CPU oracle
-def cpu_oracle_rate(psi, r, npairs, seed=0):
+def cpu_oracle_rate(psi, r, npairs, seed=0, periodic=False):
     """Time the FP64 oracle on a seeded sample of the workload's pair solves
-    (co-density, padded FFT Poisson solve, E_ij, both V psi products)."""
+    (co-density, FFT Poisson solve, E_ij, both V psi products)."""
     import numpy as np
     from oracle import exx_oracle as o
-    Gh = o.kernel_spectrum(o.kernel_real_space(r.n, r.h))
+    Gh = (o.kernel_spectrum_periodic(r.n, r.h) if periodic
+          else o.kernel_spectrum(o.kernel_real_space(r.n, r.h)))
     rng = np.random.default_rng(seed)
     pairs = o.pair_list(r.norb)
     pick = [pairs[k] for k in rng.choice(len(pairs), size=npairs, replace=False)]
@@ -313,7 +318,9 @@ def run_ours(a):
     N, n = r.norb, r.n
     P = N * (N + 1) // 2
     occ = np.full(N, r.occupation)
-    plan = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp32")
+    per = a.bc == "periodic"
+    kern = "periodic" if per else "sinc"
+    plan = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp32", kernel=kern)
     info = plan.info()
     out = torch.empty(psi.shape, dtype=torch.float32, device=dev)
     E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -353,7 +360,7 @@ def run_ours(a):
     ms_step = ms / a.steps
 
     # roofline of the dominant kernel
-    alg = algorithmic_bytes(n, N, info["tile"])
+    alg = algorithmic_bytes(n, N, info["tile"], periodic=per)
     dom = max(alg, key=lambda k: prof[k][0])
     kms, kcnt = prof[dom]
     per_launch_bytes = alg[dom] / (kcnt / a.steps)
@@ -368,15 +375,18 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": a.workload, "norb": N, "n": n, "padded": 2 * n, "h": r.h,
+            "config": {"workload": a.workload, "bc": a.bc, "norb": N, "n": n,
+                       "fft_grid": n if per else 2 * n, "h": r.h,
                        "pairs": P, "tile": info["tile"], "precision": "fp32 ffts, fp64 reductions",
-                       "l2": "inputs larger than L2 (psi 226 MB; 0.9 GB pair-tile spectra)",
+                       "l2": "inputs larger than L2 (psi 226 MB; pair-tile spectra 0.2-0.9 GB)",
                        "parallelism": f"replicas x{world}"},
             "E_x": E, "clocks": clocks, "roofline": roofline,
             "gpu_launches": info["launches_apply"] * a.steps}
+    if per:
+        line["roofline"]["traffic"] = None  # the committed capture is of the free-BC kernels
 
     golden = os.path.join(ROOT, "tests", "golden", f"{a.workload}.json")
-    if a.norb:
+    if a.norb or per:
         golden = ""
     if os.path.exists(golden):
         with open(golden) as fh:
@@ -428,7 +438,7 @@ def run_ours(a):
 
     # FP64 plain GPU path on the same workload (the comparison the metric names)
     if not a.no_fp64 and not big:
-        p64 = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp64")
+        p64 = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp64", kernel=kern)
         psi64 = torch.from_numpy(psi_np).to(dev)
         out64 = torch.empty(psi64.shape, dtype=torch.float64, device=dev)
         p64.apply_async(psi64, out64, E_dev)
@@ -458,7 +468,7 @@ def run_ours(a):
         if big:
             psi_np = psi.double().cpu().numpy()
         a.cpu_sample = sample
-        rate, dt = cpu_oracle_rate(psi_np, r, a.cpu_sample)
+        rate, dt = cpu_oracle_rate(psi_np, r, a.cpu_sample, periodic=per)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle", "seconds": dt,
                                 "sample": f"{a.cpu_sample} seeded pair solves (of {P}) of the same "
