@@ -49,7 +49,10 @@ typedef enum {
   EXX_ERR_INVALID_ARG = 1,   /* NULL pointer, n < 2, h <= 0, norb < 1, bad enum */
   EXX_ERR_CUDA = 2,          /* a CUDA runtime call failed (see exx_last_error)  */
   EXX_ERR_OOM = 3,           /* device workspace could not be allocated          */
-  EXX_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up               */
+  EXX_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up (reported by
+                                the next synchronising call: exx_energy,
+                                exx_apply with E_out, exx_apply_host,
+                                exx_batch_pair_energies)                         */
   EXX_ERR_NOT_SUPPORTED = 5  /* non-cubic grid, 2n with a prime factor > 7, or a
                                 size beyond the compiled kernels                  */
 } exx_status_t;
@@ -203,7 +206,8 @@ exx_status_t exx_profile_read(exx_plan_t plan, double* ms, long long* launches, 
  *   n, h, kernel   grid points per axis (2 <= n <= EXX_NOALLOC_MAX_N), spacing,
  *                  exx_kernel_t.
  *   psi            device, float [norb][n][n][n]; orbitals i and j are used.
- *   E_dev          device, one double, receives E_ij (no host copy, no sync).
+ *   E_dev          device, one double, receives E_ij (no host copy, no sync);
+ *                  NaN if a bounded device-side wait of the call ran out.
  * Scratch is a set of file-scope device arrays sized for EXX_NOALLOC_MAX_N
  * (about 29 MB, held by every GPU that loads the library until the process
  * exits).  n > EXX_NOALLOC_MAX_N returns EXX_ERR_NOT_SUPPORTED, as does a grid

@@ -209,6 +209,8 @@ struct exx_plan_s {
   void* V = nullptr;
   double* vacc = nullptr;
   double* E_dev = nullptr;
+  int* d_err = nullptr;    // set by a device-side wait that ran out
+  CUtensorMap gmap{};      // TMA descriptor of the kernel table (Ops::stage_table)
   void* h_psi = nullptr;  // exx_apply_host staging (allocated on first use)
   void* h_vx = nullptr;
   // per-kernel event timing (exx_profile_enable)
@@ -236,8 +238,8 @@ exx_status_t cuda_fail(exx_plan_t p, cudaError_t e) {
   } while (0)
 
 void free_plan(exx_plan_t p) {
-  void* ptrs[] = {p->Gs,    p->tw, p->d_occ, p->d_pairs, p->epart, p->Epair, p->X2,
-                  p->V,     p->vacc, p->E_dev, p->h_psi, p->h_vx};
+  void* ptrs[] = {p->Gs, p->tw,   p->d_occ, p->d_pairs, p->epart, p->Epair, p->X2,
+                  p->V,  p->vacc, p->E_dev, p->d_err,   p->h_psi, p->h_vx};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int k = 0; k < EXX_NKINDS; ++k)
@@ -474,6 +476,7 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
     EXX_ALLOC(p->vacc, (size_t)norb * n3 * sizeof(double));
   }
   EXX_ALLOC(p->E_dev, sizeof(double));
+  EXX_ALLOC(p->d_err, sizeof(int));
 #undef EXX_ALLOC
 
   cudaError_t e = cudaMemcpyAsync(p->Gs, gbuf.data(), gbuf.size(), cudaMemcpyHostToDevice, st);
@@ -483,7 +486,10 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_pairs, pairs.data(), pairs.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&p->gmap, p->Gs, nh))
+    e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = ops->setup();
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -542,7 +548,7 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
     }
     {
       ProfScope ps(p, K_ZCONV, st);
-      p->ops->zconv(p->X2, p->Gs, p->tw, p->epart, t.count, !apply, st);
+      p->ops->zconv(p->X2, p->Gs, p->tw, &p->gmap, p->epart, p->d_err, t.count, !apply, st);
     }
     {
       ProfScope ps(p, K_PAIRE, st);
@@ -595,14 +601,25 @@ exx_status_t exx_energy_async(exx_plan_t p, const void* psi, double* E_dev, void
   return run(p, psi, nullptr, E_dev, false, static_cast<cudaStream_t>(cuda_stream));
 }
 
+// A bounded device-side wait that ran out leaves a flag; the synchronising
+// calls report it as EXX_ERR_TIMEOUT (and clear it).
+static exx_status_t check_wait_flag(exx_plan_t p, cudaStream_t st) {
+  int f = 0;
+  EXX_CUDA(p, cudaMemcpyAsync(&f, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  EXX_CUDA(p, cudaStreamSynchronize(st));
+  if (f == 0) return EXX_OK;
+  EXX_CUDA(p, cudaMemsetAsync(p->d_err, 0, sizeof(int), st));
+  p->err = "a device-side wait ran out (kernel-table copy)";
+  return EXX_ERR_TIMEOUT;
+}
+
 exx_status_t exx_apply(exx_plan_t p, const void* psi, void* vxpsi, double* E_out, void* cuda_stream) {
   if (p == nullptr || psi == nullptr || vxpsi == nullptr) return EXX_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   exx_status_t s = run(p, psi, vxpsi, nullptr, true, st);
   if (s != EXX_OK || E_out == nullptr) return s;
   EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
-  EXX_CUDA(p, cudaStreamSynchronize(st));
-  return EXX_OK;
+  return check_wait_flag(p, st);
 }
 
 exx_status_t exx_energy(exx_plan_t p, const void* psi, double* E_out, void* cuda_stream) {
@@ -611,8 +628,7 @@ exx_status_t exx_energy(exx_plan_t p, const void* psi, double* E_out, void* cuda
   exx_status_t s = run(p, psi, nullptr, nullptr, false, st);
   if (s != EXX_OK) return s;
   EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
-  EXX_CUDA(p, cudaStreamSynchronize(st));
-  return EXX_OK;
+  return check_wait_flag(p, st);
 }
 
 exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host, double* E_out,
@@ -635,8 +651,7 @@ exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host
   if (s != EXX_OK) return s;
   EXX_CUDA(p, cudaMemcpyAsync(vxpsi_host, p->h_vx, cnt * vs, cudaMemcpyDeviceToHost, st));
   if (E_out) EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
-  EXX_CUDA(p, cudaStreamSynchronize(st));
-  return EXX_OK;
+  return check_wait_flag(p, st);
 }
 
 exx_status_t exx_profile_enable(exx_plan_t p, int enable) {

@@ -95,6 +95,7 @@ struct Group {
   std::vector<Wave> waves;
   void* Gs = nullptr;
   void* tw = nullptr;
+  CUtensorMap gmap{};  // TMA descriptor of Gs (ops->stage_table)
 };
 
 struct Mol {
@@ -124,6 +125,7 @@ struct exx_batch_s {
   double* d_occ = nullptr;
   double* Epair = nullptr;
   double* epart = nullptr;
+  int* d_err = nullptr;  // set by a device-side wait that ran out
   void* X = nullptr;
   void* V = nullptr;
   double* vacc = nullptr;
@@ -146,8 +148,9 @@ struct exx_batch_s {
 namespace {
 
 void batch_free(exx_batch_t b) {
-  void* ptrs[] = {b->d_pairs, b->d_tiles, b->d_occ, b->Epair, b->epart, b->X, b->V, b->vacc,
-                  b->d_mt, (void*)b->d_psi_tab, b->d_vacc_tab, b->d_vx_tab, b->d_count};
+  void* ptrs[] = {b->d_pairs, b->d_tiles, b->d_occ,  b->Epair,           b->epart,
+                  b->X,       b->V,       b->vacc,   b->d_mt,            (void*)b->d_psi_tab,
+                  b->d_vacc_tab, b->d_vx_tab, b->d_count, b->d_err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (Group& g : b->groups) {
@@ -183,7 +186,7 @@ exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, cudaStream_t st) 
       const int4* pr = b->d_pairs + w.pair_off;
       g.ops->fwd_xy(nullptr, reinterpret_cast<const void* const*>(b->d_psi_tab), pr, w.npair, b->X,
                     g.tw, n3, st);
-      g.ops->zconv(b->X, g.Gs, g.tw, b->epart, w.npair, !apply, st);
+      g.ops->zconv(b->X, g.Gs, g.tw, &g.gmap, b->epart, b->d_err, w.npair, !apply, st);
       k_pair_energy<<<(w.npair * 32 + 255) / 256, 256, 0, st>>>(b->epart, nper, pr, w.npair, h3,
                                                                  b->Epair);
       if (apply) {
@@ -433,8 +436,16 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
     up(g.Gs, gf.data(), gf.size());
     up(g.tw, tw.data(), tw.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host buffers die at scope end
+    if (e == cudaSuccess && g.ops->stage_table && !exx::make_ktab_map(&g.gmap, g.Gs, g.n))
+      e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = g.ops->setup();
   }
+  if (!balloc(b, &b->d_err, sizeof(int))) {
+    batch_free(b);
+    delete b;
+    return EXX_ERR_OOM;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -504,11 +515,17 @@ exx_status_t exx_batch_pair_energies(exx_batch_t b, int mol, double* out_host, v
   if (b == nullptr || out_host == nullptr || mol < 0 || mol >= b->nmol) return EXX_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const Mol& m = b->mol[mol];
+  int flag = 0;
   if (cudaMemcpyAsync(out_host, b->Epair + m.ep_off, (size_t)m.P * sizeof(double),
                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return EXX_ERR_CUDA;
+  }
+  if (flag) {  // a bounded device-side wait ran out
+    cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
+    return EXX_ERR_TIMEOUT;
   }
   return EXX_OK;
 }

@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda.h>  // CUtensorMap
 
 #include "exx_fft.cuh"
 
@@ -72,15 +73,53 @@ template <int P, bool FULL, typename C> EXX_HD void dft_inv_out(C* v) {
   else dft_halfout<P, 1>(v);
 }
 
-// 16-byte asynchronous global -> shared copy (cp.async); src_bytes = 0 fills
-// the destination with zeros without reading.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+// Tensor-memory-access (TMA) load with an mbarrier (PTX, sm_90 and later).
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  // make the initialisation visible to the asynchronous (TMA) proxy
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 3-D tiled load of the box at coordinates (c0, c1, c2) (c0 innermost) of the
+// tensor map into shared memory; completion is counted on bar in bytes.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait for the completion of phase `parity` of bar, polling at most `limit`
+// times; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+constexpr int kWaitPolls = 1 << 20;  // bound of every device-side wait
+
+// byte offset of zconv's staged kernel-table slice: after the twiddles and the
+// column buffer, rounded up to 128 bytes
+__host__ __device__ constexpr size_t zconv_gsm_offset(int L, int W, size_t cs) {
+  return ((size_t)(L + L * W) * cs + 127) / 128 * 128;
+}
 
 // Kernel table of zconv (built by build_kernel_table): Gt[kx][kz][ky],
 // kx <= n, kz, ky < 2n, the scaled kernel spectrum divided by the energy
@@ -311,14 +350,14 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 // length L1 over z = L2 n1 + n2, pass 2 of length L2), multiply by the kernel
 // table (Ghat/(2n)^3) with the Parseval energy w(kx) Ghat |rho_hat|^2, inverse
 // FFT keeping z < n.  In place on X.  STAGE: the CTA's slice of the kernel
-// table, Gt[kx][kz][ky0 .. ky0 + W), is copied to shared memory by
-// asynchronous 16-byte copies that overlap the first pass (FP32 rows aligned
-// to 16 bytes, and only where it costs no occupancy); otherwise the values
-// are read from global memory in the second pass.
+// table, Gt[kx][kz][ky0 .. ky0 + W), is brought into shared memory by one TMA
+// load (tensor map gmap, box W x 2n x 1) that overlaps the first pass (FP32,
+// and only where it costs no occupancy); otherwise the values are read from
+// global memory in the second pass.  A wait that runs out sets *err.
 template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool PER, bool ENERGY_ONLY>
 __global__ void __launch_bounds__(32 * NW, MINB)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
-        double* __restrict__ epart) {
+        double* __restrict__ epart, const __grid_constant__ CUtensorMap gmap, int* __restrict__ err) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int W = L < 32 ? L : 32;
@@ -326,13 +365,31 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);  // w^k [L]
   C* buf = tw + L;                         // [L slots][W]
-  R* gsm = reinterpret_cast<R*>(buf + L * W);  // [L][W] (STAGE)
+  // [L][W] (STAGE): the TMA destination, 128-byte aligned in the shared window
+  // (the dynamic allocation starts after the static variables, so the base is
+  // aligned at run time; the allocation has 128 bytes of slack for this)
+  R* gsm = reinterpret_cast<R*>(smem_raw + zconv_gsm_offset(L, W, sizeof(C)) +
+                                ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   __shared__ double red[NW];
+  __shared__ __align__(8) unsigned long long gbar;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int yb = blockIdx.x, kx = blockIdx.y, p = blockIdx.z;
   const int ky = yb * W + lane;
   const bool valid = lane < W && ky < L;
+  if constexpr (STAGE) {
+    static_assert(sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 && L <= 256, "TMA box");
+    if (tid == 0) {  // out-of-range ky of a partial last block read as zero
+      mbar_init(&gbar, 1);
+      if ((smem_u32(gsm) & 127u) == 0) {
+        mbar_expect_tx(&gbar, (unsigned)(L * W * sizeof(R)));
+        tma_load_3d(gsm, &gmap, yb * W, 0, kx, &gbar);
+      } else {  // never expected: report instead of issuing an unaligned copy
+        atomicExch(err, 2);
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&gbar)) : "memory");
+      }
+    }
+  }
   for (int t = tid; t < L; t += 32 * NW) tw[t] = tw_g[t];
   constexpr int GR = FOLDY ? N + 1 : L;  // table row length
   const int kyt = FOLDY ? (ky <= N ? ky : L - ky) : ky;
@@ -343,17 +400,6 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
     if (valid)
       cyl = reinterpret_cast<const double*>(reinterpret_cast<const unsigned char*>(Gs) +
                                             ktab_cy_offset(N, sizeof(R)))[ky];
-  }
-  if constexpr (STAGE) {
-    static_assert((W * sizeof(R)) % 16 == 0 && (L * sizeof(R)) % 16 == 0, "unaligned rows");
-    constexpr int VPR = 16 / sizeof(R), RPR = W / VPR;  // values / requests per row
-    for (int t = tid; t < L * RPR; t += 32 * NW) {
-      const int kz = t / RPR, c = (t - kz * RPR) * VPR;
-      const int k0 = yb * W + c;  // first ky of the request; L % VPR == 0
-      cp_async16(gsm + kz * W + c, Gs + ((long long)kx * L + kz) * L + (k0 < L ? k0 : 0),
-                 k0 < L ? 16 : 0);
-    }
-    cp_async_commit();
   }
   constexpr int G = PER ? 2 * N : N;  // z planes stored (grid points per axis)
   constexpr int NIN = PER ? L1 : H1;   // nonzero inputs / kept outputs per DFT_L1
@@ -374,7 +420,9 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
         buf[(n2 * L1 + k1) * W + lane] = cmul(v[k1], tw[n2 * k1]);
     }
   }
-  if constexpr (STAGE) cp_async_wait_all();  // own copies done; the barrier publishes all
+  if constexpr (STAGE) {
+    if (!mbar_wait(&gbar, 0, kWaitPolls)) atomicExch(err, 1);
+  }
   __syncthreads();
 
   // forward pass 2, kernel multiply, energy, inverse pass 1

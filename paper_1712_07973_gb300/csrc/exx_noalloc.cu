@@ -47,6 +47,7 @@ static __device__ __align__(256) float g_noalloc_kern[kKernElems];
 static __device__ __align__(256) float2 g_noalloc_tw[kTwElems];
 static __device__ __align__(256) double g_noalloc_epart[kEpartElems];
 static __device__ __align__(256) int4 g_noalloc_pair[1];
+static __device__ int g_noalloc_err[1];  // set by a device-side wait that ran out (zero at load)
 
 namespace {
 
@@ -61,6 +62,8 @@ struct DeviceScratch {
   float2* tw = nullptr;
   double* epart = nullptr;
   int4* pair = nullptr;
+  int* err = nullptr;
+  CUtensorMap gmap{};  // TMA descriptor of the kernel table (ops->stage_table)
   int n = 0;
   double h = 0.0;
   int kind = -1;
@@ -71,14 +74,18 @@ DeviceScratch g_noalloc_dev[kMaxDevices];
 
 __global__ void k_noalloc_set_pair(int i, int j) { g_noalloc_pair[0] = make_int4(i, j, 0, 0); }
 
-// E = h^3 * (sum of the column-block partials), fixed-order warp reduction
+// E = h^3 * (sum of the column-block partials), fixed-order warp reduction;
+// NaN (and the flag cleared) when a device-side wait of this pair ran out
 __global__ void k_noalloc_pair_total(const double* __restrict__ epart, int nper, double h3,
-                                     double* __restrict__ E) {
+                                     int* __restrict__ err, double* __restrict__ E) {
   double s = 0.0;
   for (int t = threadIdx.x; t < nper; t += 32) s += epart[t];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (threadIdx.x == 0) *E = h3 * s;
+  if (threadIdx.x == 0) {
+    *E = *err ? __longlong_as_double(0x7ff8000000000000LL) : h3 * s;
+    *err = 0;
+  }
 }
 
 // One-time set-up on the current device: device addresses of the arrays.
@@ -87,7 +94,8 @@ exx_status_t lookup_addresses(DeviceScratch& d) {
       cudaGetSymbolAddress(reinterpret_cast<void**>(&d.kern), g_noalloc_kern) != cudaSuccess ||
       cudaGetSymbolAddress(reinterpret_cast<void**>(&d.tw), g_noalloc_tw) != cudaSuccess ||
       cudaGetSymbolAddress(reinterpret_cast<void**>(&d.epart), g_noalloc_epart) != cudaSuccess ||
-      cudaGetSymbolAddress(reinterpret_cast<void**>(&d.pair), g_noalloc_pair) != cudaSuccess) {
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&d.pair), g_noalloc_pair) != cudaSuccess ||
+      cudaGetSymbolAddress(reinterpret_cast<void**>(&d.err), g_noalloc_err) != cudaSuccess) {
     cudaGetLastError();
     return EXX_ERR_CUDA;
   }
@@ -114,6 +122,8 @@ exx_status_t load_tables(DeviceScratch& d, const exx::Ops* ops, int n, double h,
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&d.gmap, d.kern, n))
+    e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = ops->setup();
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -163,8 +173,8 @@ extern "C" exx_status_t exx_pair_energy_noalloc(int n, double h, int kernel, con
   const long long n3 = (long long)n * n * n;
   k_noalloc_set_pair<<<1, 1, 0, st>>>(i, j);
   ops->fwd_xy(psi, nullptr, d->pair, 1, d->spec, d->tw, n3, st);
-  ops->zconv(d->spec, d->kern, d->tw, d->epart, 1, true, st);
-  k_noalloc_pair_total<<<1, 32, 0, st>>>(d->epart, (n + 1) * ops->nyb, h * h * h, E_dev);
+  ops->zconv(d->spec, d->kern, d->tw, &d->gmap, d->epart, d->err, 1, true, st);
+  k_noalloc_pair_total<<<1, 32, 0, st>>>(d->epart, (n + 1) * ops->nyb, h * h * h, d->err, E_dev);
   if (cudaGetLastError() != cudaSuccess) return EXX_ERR_CUDA;
   return EXX_OK;
 }

@@ -6,6 +6,9 @@
 #include <cmath>
 #include <cstddef>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "exx_gain.cuh"
 #include "exx_kernels.cuh"
 
@@ -28,8 +31,11 @@ struct Ops {
   // molecule slot) may be null, in which case every pair reads psi
   void (*fwd_xy)(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
                  void* X, const void* tw, long long n3, cudaStream_t st) = nullptr;
-  void (*zconv)(void* X, const void* Gs, const void* tw, double* epart, int npair,
-                bool energy_only, cudaStream_t st) = nullptr;
+  // gmap: TMA descriptor of the kernel table (make_ktab_map; read only when
+  // stage_table); err: device flag set by a wait that ran out
+  void (*zconv)(void* X, const void* Gs, const void* tw, const CUtensorMap* gmap, double* epart,
+                int* err, int npair, bool energy_only, cudaStream_t st) = nullptr;
+  bool stage_table = false;
   void (*inv_yx)(const void* X3, void* V, const void* tw, int npair, cudaStream_t st) = nullptr;
 };
 
@@ -67,6 +73,31 @@ constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_
   size_t q = (kSmemPerCTA - fixed) / line;
   q = q > 64 ? 64 : q;
   return SlabShape{(int)q, 640, 1, 1, fixed + q * line, true};
+}
+
+// TMA descriptor of an FP32 zconv kernel table Gt[kx][kz][ky] (unfolded layout,
+// kx <= n, kz, ky < 2n): 3-D, box of min(2n, 32) ky by 2n kz by one kx, no
+// swizzle, out-of-range elements read as zero.  The driver's encoder is
+// reached through the runtime (no link against the driver library).
+inline bool make_ktab_map(CUtensorMap* map, const void* table, int n) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (encode == nullptr) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t L = 2 * (cuuint64_t)n;
+  const cuuint64_t dims[3] = {L, L, (cuuint64_t)n + 1};
+  const cuuint64_t strides[2] = {L * sizeof(float), L * L * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)(L < 32 ? L : 32), (cuuint32_t)L, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(table), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Launch of a slab kernel; CL > 1 launches (CL, 1, 1) thread-block clusters.
@@ -184,9 +215,11 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
   // fit in an SM's 228 KB of shared memory
   static constexpr size_t smem_b0 = ((size_t)L + (size_t)L * W) * sizeof(C);
   static constexpr size_t smem_g = (size_t)L * W * sizeof(R);
+  static constexpr size_t smem_bg = zconv_gsm_offset(L, W, sizeof(C)) + smem_g + 128;  // + alignment slack
   static constexpr bool stage_g = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 &&
-                                  (L * sizeof(R)) % 16 == 0 && 3 * (smem_b0 + smem_g + 1024) <= 228 * 1024;
-  static constexpr size_t smem_b = smem_b0 + (stage_g ? smem_g : 0);
+                                  (L * sizeof(R)) % 16 == 0 && L <= 256 &&
+                                  3 * (smem_bg + 1024) <= 228 * 1024;
+  static constexpr size_t smem_b = stage_g ? smem_bg : smem_b0;
   // CTAs per SM the zconv register budget is sized for: three where shared
   // memory allows (FP32), else two
   static constexpr int MINB_B = (sizeof(R) == 4 && 3 * (smem_b + 1024) <= 228 * 1024) ? 3 : 2;
@@ -219,16 +252,20 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
                         reinterpret_cast<const R* const*>(psi_tab), pairs, static_cast<C*>(X),
                         static_cast<const C*>(tw), n3);
   }
-  static void zconv(void* X, const void* Gs, const void* tw, double* epart, int npair,
-                    bool energy_only, cudaStream_t st) {
+  static void zconv(void* X, const void* Gs, const void* tw, const CUtensorMap* gmap,
+                    double* epart, int* err, int npair, bool energy_only, cudaStream_t st) {
     if constexpr (ok) {
       const dim3 grid(NYB, N + 1, npair);
+      CUtensorMap m{};
+      if (stage_g && gmap) m = *gmap;
       if (energy_only)
         k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, true><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
+            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, m,
+            err);
       else
         k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, false><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart);
+            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, m,
+            err);
     }
   }
   static void inv_yx(const void* X, void* V, const void* tw, int npair, cudaStream_t st) {
@@ -252,6 +289,7 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
     o.smem_c = smem_c;
     o.setup = &setup;
     o.table_fold_y = fold_y;
+    o.stage_table = stage_g;
     if constexpr (ok && sizeof(R) == 4) o.gains = &GainModel<N, PER>::gains;
     o.fwd_xy = &fwd_xy;
     o.zconv = &zconv;
