@@ -476,7 +476,7 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
     EXX_ALLOC(p->vacc, (size_t)norb * n3 * sizeof(double));
   }
   EXX_ALLOC(p->E_dev, sizeof(double));
-  EXX_ALLOC(p->d_err, sizeof(int));
+  EXX_ALLOC(p->d_err, 2 * sizeof(int));
 #undef EXX_ALLOC
 
   cudaError_t e = cudaMemcpyAsync(p->Gs, gbuf.data(), gbuf.size(), cudaMemcpyHostToDevice, st);
@@ -486,7 +486,17 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_pairs, pairs.data(), pairs.size() * sizeof(int4), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, 2 * sizeof(int), st);
+  // test hook (EXX_TEST_STALL_TABLE_COPY=1): the staged kernel-table copy is
+  // never issued, so its bounded wait runs out and exx_energy returns
+  // EXX_ERR_TIMEOUT; the context stays usable
+  if (e == cudaSuccess && ops->stage_table) {
+    const char* hook = std::getenv("EXX_TEST_STALL_TABLE_COPY");
+    if (hook != nullptr && hook[0] == '1') {
+      static const int one = 1;
+      e = cudaMemcpyAsync(p->d_err + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&p->gmap, p->Gs, nh))
     e = cudaErrorInvalidValue;

@@ -440,12 +440,12 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
       e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = g.ops->setup();
   }
-  if (!balloc(b, &b->d_err, sizeof(int))) {
+  if (!balloc(b, &b->d_err, 2 * sizeof(int))) {
     batch_free(b);
     delete b;
     return EXX_ERR_OOM;
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 2 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -47,7 +47,7 @@ static __device__ __align__(256) float g_noalloc_kern[kKernElems];
 static __device__ __align__(256) float2 g_noalloc_tw[kTwElems];
 static __device__ __align__(256) double g_noalloc_epart[kEpartElems];
 static __device__ __align__(256) int4 g_noalloc_pair[1];
-static __device__ int g_noalloc_err[1];  // set by a device-side wait that ran out (zero at load)
+static __device__ int g_noalloc_err[2];  // [0] set by a device-side wait that ran out; [1] test hook
 
 namespace {
 

@@ -32,7 +32,8 @@ struct Ops {
   void (*fwd_xy)(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
                  void* X, const void* tw, long long n3, cudaStream_t st) = nullptr;
   // gmap: TMA descriptor of the kernel table (make_ktab_map; read only when
-  // stage_table); err: device flag set by a wait that ran out
+  // stage_table); err: two device ints, [0] set by a wait that ran out, [1] a
+  // test hook that makes the staged copy's wait run out
   void (*zconv)(void* X, const void* Gs, const void* tw, const CUtensorMap* gmap, double* epart,
                 int* err, int npair, bool energy_only, cudaStream_t st) = nullptr;
   bool stage_table = false;

@@ -357,3 +357,25 @@ def test_periodic_fp32_192(torch_dev):
     assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6, (E, Ee, Eo)
     assert np.max(np.abs(Eij - Eijo)) <= 1e-6
     assert np.max(np.abs(vx - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+
+
+def test_bounded_wait_times_out_and_context_survives(torch_dev, monkeypatch):
+    # zconv waits on its staged kernel-table copy with a bounded poll count;
+    # the test hook withholds the copy (no GPU fault, no endless loop), so the
+    # wait runs out, the synchronising call returns EXX_ERR_TIMEOUT and the
+    # context stays usable
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    psi = _orbitals(8, 2, seed=5)
+    occ = np.full(2, 2.0)
+    monkeypatch.setenv("EXX_TEST_STALL_TABLE_COPY", "1")
+    plan = exx.ExxPlan(8, 0.45, 0.25, occ, precision="fp32")
+    monkeypatch.delenv("EXX_TEST_STALL_TABLE_COPY")
+    p = torch.from_numpy(psi).to(dev, torch.float32)
+    with pytest.raises(exx.ExxError) as ei:
+        plan.energy(p)
+    assert "EXX_ERR_TIMEOUT" in str(ei.value)
+    plan.close()
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, 0.25, 0.45, "fp32")
+    Eo, _, _ = _oracle(psi, occ, 0.25, 0.45)
+    assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6
