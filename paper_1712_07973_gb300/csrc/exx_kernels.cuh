@@ -431,7 +431,15 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 
   // forward pass 2, kernel multiply, energy, inverse pass 1
   double eacc = 0.0;
+  // PF (unstaged, with the register budget of two CTAs per SM): the unit's
+  // kernel-table values are requested before its transform
+  constexpr bool PF = !STAGE && MINB <= 2 && sizeof(R) == 4;
   for (int k1 = warp; k1 < L1; k1 += NW) {
+    R gp[PF ? L2 : 1];
+    if constexpr (PF) {
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) gp[k2] = valid ? __ldg(Gk + (k1 + L1 * k2) * GR) : R(0);
+    }
     C v[L2];
 #pragma unroll
     for (int n2 = 0; n2 < L2; ++n2)
@@ -443,6 +451,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
       const int kz = k1 + L1 * k2;
       R gv;
       if constexpr (STAGE) gv = valid ? gsm[kz * W + lane] : R(0);  // lane < W
+      else if constexpr (PF) gv = gp[k2];
       else gv = valid ? __ldg(Gk + kz * GR) : R(0);
       es += gv * (sq(v[k2].x) + sq(v[k2].y));
       v[k2] = cscale(v[k2], gv);
