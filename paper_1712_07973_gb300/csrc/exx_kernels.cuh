@@ -278,12 +278,30 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
     constexpr int NWP = NT / 32;
     const int lane = tid & 31, hr = lane >> 4, cl16 = lane & 15;
     C* Sw = S + ((tid >> 5) * 2 + hr) * Scr<L1, L2>::line;
+    // a lane's first pass-1 unit is n2 = cl16 in every row it transforms: in
+    // FP32 its twiddles stay in registers (FP64 lacks the registers)
+    constexpr bool TWR = sizeof(R) == 4;
+    C twr[TWR ? L1 : 1];
+    if constexpr (TWR) {
+#pragma unroll
+      for (int k1 = 1; k1 < L1; ++k1) twr[k1] = cl16 < L2 ? ty[k1 * L2 + cl16] : mkc<C>(R(0), R(0));
+    }
     for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 <= N; r0 += 2 * NWP * CL) {
       const int kx = r0 + hr;
       const bool rv = kx <= N;
-      for (int n2 = cl16; n2 < L2; n2 += 16) {
+      const int rb = srow<SP, X1>(kx);
+      if (rv && cl16 < L2) {
+        C v[L1];
+#pragma unroll
+        for (int n1 = 0; n1 < NIN; ++n1) v[n1] = (n1 < NB ? h0 : h1)[rb + L2 * (n1 % NB) + cl16];
+        dft_fwd_in<L1, PER>(v);
+        C* o = Sw + cl16 * Scr<L1, L2>::row;
+        o[0] = v[0];
+#pragma unroll
+        for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul(v[k1], TWR ? twr[TWR ? k1 : 0] : ty[k1 * L2 + cl16]);
+      }
+      for (int n2 = cl16 + 16; n2 < L2; n2 += 16) {  // L2 > 16: further units
         if (rv) {
-          const int rb = srow<SP, X1>(kx);
           C v[L1];
 #pragma unroll
           for (int n1 = 0; n1 < NIN; ++n1) v[n1] = (n1 < NB ? h0 : h1)[rb + L2 * (n1 % NB) + n2];
