@@ -569,6 +569,14 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
     constexpr int NWP = NT / 32;
     const int lane = tid & 31, hr = lane >> 4, cl16 = lane & 15;
     C* Sw = S + ((tid >> 5) * 2 + hr) * Scr<L1, L2>::line;
+    // a lane's pass-1 unit is k1 = cl16 in every row: in FP32 its twiddles
+    // stay in registers
+    constexpr bool TWR = sizeof(R) == 4;
+    C twr[TWR ? L2 : 1];
+    if constexpr (TWR) {
+#pragma unroll
+      for (int m2 = 1; m2 < L2; ++m2) twr[m2] = cl16 < L1 ? ti[m2 * L1 + cl16] : mkc<C>(R(0), R(0));
+    }
     for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 <= N; r0 += 2 * NWP * CL) {
       const int kx = r0 + hr;
       const bool rv = kx <= N;
@@ -581,7 +589,8 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
         C* q = Sw + cl16;
         q[0] = v[0];
 #pragma unroll
-        for (int m2 = 1; m2 < L2; ++m2) q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], ti[m2 * L1 + cl16]);
+        for (int m2 = 1; m2 < L2; ++m2)
+          q[m2 * Scr<L1, L2>::row] = cmulc(v[m2], TWR ? twr[TWR ? m2 : 0] : ti[m2 * L1 + cl16]);
       }
       __syncwarp();
       for (int m2 = cl16; m2 < L2; m2 += 16) {
