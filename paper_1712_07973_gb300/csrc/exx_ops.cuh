@@ -44,9 +44,10 @@ constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation 
 
 // Launch shape of the slab kernels (fwd_xy, inv_yx): shared memory = fixed
 // part (slab + twiddles) + y-pass scratch.  In order of preference:
-//   warp-owned y passes (q = 0, two scratch rows per warp) as two CTAs of 320
-//   threads per SM when asked for and they fit in half an SM, else one CTA
-//   of 640;
+//   warp-owned y passes (q = 0, two scratch rows per warp) as four CTAs of
+//   160 threads per SM when asked for and they fit in a quarter of an SM
+//   (small slabs: periodic 96^3 -6.6% per exx_apply against two CTAs of 320),
+//   two CTAs of 320 when they fit in half an SM, else one CTA of 640;
 //   the same with the slab split over a two-CTA cluster (cl = 2, half the
 //   columns per CTA; fixed2 is its fixed part), when allowed;
 //   CTA-wide batches of q rows.
@@ -61,6 +62,8 @@ struct SlabShape {
 constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_t line,
                                bool prefer_two) {
   const size_t half = 113 * 1024;
+  if (prefer_two && fixed + 10 * line <= 56 * 1024)  // small slabs: four CTAs of 160
+    return SlabShape{0, 160, 4, 1, fixed + 10 * line, true};
   if (prefer_two && fixed + 20 * line <= half) return SlabShape{0, 320, 2, 1, fixed + 20 * line, true};
   if (fixed + 40 * line <= kSmemPerCTA) return SlabShape{0, 640, 1, 1, fixed + 40 * line, true};
   if (split_ok && fixed2 + 40 * line <= kSmemPerCTA)
