@@ -11,7 +11,7 @@
 //           along z: pruned forward FFT (z >= n zero), multiply by the real
 //           kernel spectrum Ghat (Sec. 2.1.2; scaled by 1/(2n)^3), Parseval
 //           energy sum w(kx) Ghat |rho_hat|^2, inverse FFT keeping z < n.
-//           In place on X.
+//           In place on X.  The kernel table slice of a CTA arrives by TMA.
 //   inv_yx  (one CTA per z-slab and pair)
 //           inverse FFT along y keeping y < n, complex-to-real FFT along x
 //           keeping x < n: V_ij on the n^3 mesh.
@@ -21,6 +21,9 @@
 //           over the tile, FP64 accumulation across tiles, deterministic.
 //
 // Layouts: psi[o][z][y][x]; X[p][kx][z][ky] complex; V[p][z][y][x].
+// With periodic boundary conditions (template flag PER) the grid has 2n points
+// per axis, the lines are not padded and no transform is pruned; large slabs
+// are split over two-CTA clusters (CL = 2).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -149,8 +152,8 @@ template <typename C> EXX_HD void split_step(C zk, C zm, C w, C& xk, C& xm) {
 }
 
 // ------------------------------------------------------------------ fwd_xy
-// One CTA per (z-slab, pair).  Shared memory holds the slab Sl[k][y] (row
-// stride SP = n + 1).  x: the complex length-n FFT of z[m] = rho[2m] + i
+// One CTA per (z-slab, pair).  Shared memory holds the slab Sl[k][y] (rows
+// at srow(k), see slab_elems).  x: the complex length-n FFT of z[m] = rho[2m] + i
 // rho[2m+1] runs in place in column y of Sl, followed by the split into the
 // Hermitian half spectrum X[k], k = 0..n (row n is the Nyquist row).  y: the
 // pruned length-2n FFT per kx row, written to HBM as X[p][kx][z][ky].  Q = 0:
