@@ -49,7 +49,8 @@ constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation 
 //   (small slabs: periodic 96^3 -6.6% per exx_apply against two CTAs of 320),
 //   two CTAs of 320 when they fit in half an SM, else one CTA of 640;
 //   the same with the slab split over a two-CTA cluster (cl = 2, half the
-//   columns per CTA; fixed2 is its fixed part), when allowed;
+//   columns per CTA; fixed2 is its fixed part), when allowed, with 640 or
+//   else 320 threads per CTA;
 //   CTA-wide batches of q rows.
 // Measured at n = 96 (64 orbitals): warp-owned y passes with two CTAs per SM
 // take fwd_xy from 13.3 to 13.0 ms and inv_yx from 13.5 to 11.1 ms per
@@ -68,6 +69,8 @@ constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_
   if (fixed + 40 * line <= kSmemPerCTA) return SlabShape{0, 640, 1, 1, fixed + 40 * line, true};
   if (split_ok && fixed2 + 40 * line <= kSmemPerCTA)
     return SlabShape{0, 640, 1, 2, fixed2 + 40 * line, true};
+  if (split_ok && fixed2 + 20 * line <= kSmemPerCTA)  // e.g. FP64 n = 128
+    return SlabShape{0, 320, 1, 2, fixed2 + 20 * line, true};
   if (prefer_two && fixed + 8 * line <= half) {
     size_t q = (half - fixed) / line;
     q = q > 32 ? 32 : q;

@@ -379,3 +379,11 @@ def test_bounded_wait_times_out_and_context_survives(torch_dev, monkeypatch):
     E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, 0.25, 0.45, "fp32")
     Eo, _, _ = _oracle(psi, occ, 0.25, 0.45)
     assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6
+
+
+@pytest.mark.parametrize("n", [112, 128])
+def test_fp64_two_cta_slabs_320_threads(torch_dev, n):
+    # FP64 slabs of n = 112 and 128 only fit as two-CTA clusters of 320 threads
+    psi = _orbitals(n, 2, seed=40 + n, h=0.35)
+    occ = np.array([2.0, 1.0])
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.35, "fp64"), _oracle(psi, occ, 0.25, 0.35))
