@@ -437,9 +437,12 @@ def run_ours(a):
     del pg
 
     # FP64 plain GPU path on the same workload (the comparison the metric names)
-    if not a.no_fp64 and not big:
+    if not a.no_fp64 and (not big or n <= 128):
         p64 = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp64", kernel=kern)
-        psi64 = torch.from_numpy(psi_np).to(dev)
+        if big:  # same seeded orbitals, generated in FP64 on the device
+            psi64 = synth.workload(a.workload, dtype=np.float64, device=dev)[1].to(torch.float64)
+        else:
+            psi64 = torch.from_numpy(psi_np).to(dev)
         out64 = torch.empty(psi64.shape, dtype=torch.float64, device=dev)
         p64.apply_async(psi64, out64, E_dev)
         torch.cuda.synchronize()
@@ -453,7 +456,9 @@ def run_ours(a):
         ms64 = f0.elapsed_time(f1) / 2
         E64 = float(E_dev.item())
         line["fp64_plain"] = {"ms_per_step": ms64, "value": P / (ms64 * 1e-3), "unit": UNIT,
-                              "E_x": E64, "fp32_speedup": ms64 / ms_step}
+                              "E_x": E64, "fp32_speedup": ms64 / ms_step,
+                              "autograd_fp32_speedup": ms64 / line["autograd"]["ms_per_step"],
+                              "E_x_abs_diff_fp32_vs_fp64_Ha": abs(E - E64)}
         if os.path.exists(golden):
             with open(golden) as fh:
                 line["fp64_plain"]["E_x_abs_err_vs_oracle_Ha"] = abs(E64 - json.load(fh)["E_x"])
