@@ -43,6 +43,22 @@ Readings where the paper is silent (each is also listed in the design doc):
   V_hat(k) = 4 pi rho_hat(k) / |k|^2 for the band-limited density with the
   k = 0 term removed (a neutralising background), |k|^2 from the signed
   frequencies 2 pi m / (n h), |m| <= n/2.
+* Slab ("surface") boundary conditions: periodic in x and y with the cell
+  n h, free in z (zero-padded to 2n along z only).  Per in-plane frequency
+  k = |(k_x, k_y)| the kernel along z is the band-limited 1D Green's function
+  of d^2/dz^2 - k^2,  g(k, z) = 4 int_0^{pi/h} cos(q z) / (k^2 + q^2) dq
+  (-> (2 pi / k) e^{-k|z|} without the band limit); for k = 0 it is
+  regularised to g0(z) = 4 int_0^{pi/h} (cos(q z) - 1) / q^2 dq - 4 h / pi,
+  the constant chosen so that densities band-limited in z see exactly the
+  continuum potential -2 pi int |z - z'| rho(z') dz'.
+* Wire boundary conditions: free in x and y (zero-padded to 2n), periodic in
+  z with the cell n h.  Per axial frequency k the kernel in the (x, y) plane is
+  the band-limited 2D Green's function of lap_2 - k^2,
+  (2 pi)^-2 int over |q_d| <= pi/h of 4 pi e^{i q.r} / (k^2 + q^2) d^2q
+  (-> 2 K0(k r)); for k = 0 it is regularised to
+  (1/pi) int (e^{i q.r} - 1) / q^2 d^2q + 2 ln(pi/h) + 2 gamma - 4 Catalan / pi,
+  the constant chosen so that band-limited densities see exactly the
+  continuum potential -2 int ln|r - r'| rho(r') d^2r' (r in bohr).
 
 Precision: FP64 throughout.
 """
@@ -62,6 +78,8 @@ __all__ = [
     "kernel_real_space",
     "kernel_spectrum",
     "kernel_spectrum_periodic",
+    "kernel_spectrum_slab",
+    "kernel_spectrum_wire",
     "poisson",
     "direct_sum_potential",
     "pair_list",
@@ -213,17 +231,137 @@ def kernel_spectrum_periodic(n, h):
     return G
 
 
+# --------------------------------------------------------------------------
+# Slab and wire boundary conditions (readings in the module header)
+# --------------------------------------------------------------------------
+# Both kernels come from 4 pi / k^2 = int_0^inf (2 pi / t^3) e^{-k^2/(4t^2)} dt,
+# whose factor per axis is, on a free axis, the band-limited 1D function
+# (1/2pi) int_{-pi/h}^{pi/h} e^{-q^2/(4t^2)} cos(q x) dq = (t/sqrt(pi)) g(t h, x/h) / h
+# (g = sinc_kernel_g1d), and on a periodic axis its Fourier coefficient
+# e^{-k^2/(4t^2)} itself.  In h = 1 units (tau = t h, kappa = k h):
+#   slab, kappa > 0:  h g(k, d h) = h^2 2 sqrt(pi) int e^{-kappa^2/(4tau^2)} g(tau, d) / tau^2 dtau
+#   wire, kappa > 0:  h^2 g2(k, d h) = h^2 2 int e^{-kappa^2/(4tau^2)} g(tau, dx) g(tau, dy) / tau dtau
+# The t-integrals use the trapezoid rule in s = ln tau of the free kernel.
+_EULER_GAMMA = 0.57721566490153286061
+_CATALAN = 0.91596559417721901505
+
+
+def _s_nodes():
+    K = int(round((_S_MAX - _S_MIN) / _S_STEP))
+    s = _S_MIN + _S_STEP * np.arange(K + 1, dtype=np.float64)
+    w = np.full(s.size, _S_STEP)
+    w[0] *= 0.5
+    w[-1] *= 0.5
+    return np.exp(s), w
+
+
+def _g1d_minus_g0(t, m):
+    """g(t, m) - g(t, 0) without cancellation where t is small:
+    expm1(-t^2 m^2) - (-1)^m e^{-a^2} Re w(-t m + i a) + erfc(a), a = pi/(2t)."""
+    t = np.asarray(t, dtype=np.float64)[:, None]
+    m = np.asarray(m, dtype=np.float64)[None, :]
+    a = np.pi / (2.0 * t)
+    sign = np.where(np.mod(m, 2.0) == 0.0, 1.0, -1.0)
+    out = (np.expm1(-(t * m) ** 2) - sign * np.exp(-a * a) * np.real(sspecial.wofz(-t * m + 1j * a))
+           + sspecial.erfc(a))
+    out[:, (m == 0.0)[0]] = 0.0
+    return out
+
+
+def slab_kernel_z(n, h, kappa):
+    """K[c][d] = h g(kappa_c / h, d h) for d in [0, n]: the slab kernel along z
+    with its quadrature weight h, per in-plane frequency kappa_c = k h."""
+    kappa = np.atleast_1d(np.asarray(kappa, dtype=np.float64))
+    d = np.arange(n + 1, dtype=np.float64)
+    out = np.empty((kappa.size, n + 1))
+    pos = kappa > 0
+    if np.any(pos):
+        t, w = _s_nodes()
+        g = sinc_kernel_g1d(t, d)                      # (nt, n+1)
+        with np.errstate(over="ignore"):
+            e = np.exp(-kappa[pos, None] ** 2 / (4.0 * t[None, :] ** 2))
+        out[pos] = (e * (w / t)[None, :]) @ g * (2.0 * math.sqrt(math.pi))
+    if np.any(~pos):
+        # k = 0: 4 [ (1 - cos(K z)) / K - z Si(K z) ] - 4 / K at z = d h, K = pi / h
+        si, _ = sspecial.sici(np.pi * d)
+        out[~pos] = -(4.0 / np.pi) * np.where(d % 2 == 0, 1.0, -1.0) - 4.0 * d * si
+    return (h * h) * out
+
+
+def wire_kernel_xy(n, h, kappa):
+    """K2[c][dy][dx] = h^2 g2(kappa_c / h, (dx, dy) h) for dx, dy in [0, n]:
+    the wire kernel in the (x, y) plane with its weight h^2, per axial
+    frequency kappa_c = k h."""
+    kappa = np.atleast_1d(np.asarray(kappa, dtype=np.float64))
+    d = np.arange(n + 1, dtype=np.float64)
+    t, w = _s_nodes()
+    g = sinc_kernel_g1d(t, d)                          # (nt, n+1)
+    out = np.empty((kappa.size, n + 1, n + 1))
+    pos = kappa > 0
+    if np.any(pos):
+        with np.errstate(over="ignore"):
+            e = np.exp(-kappa[pos, None] ** 2 / (4.0 * t[None, :] ** 2)) * w[None, :]
+        gg = (g[:, :, None] * g[:, None, :]).reshape(t.size, -1)
+        out[pos] = (2.0 * (e @ gg)).reshape(-1, n + 1, n + 1)
+    if np.any(~pos):
+        # k = 0: g(t,dx) g(t,dy) - g(t,0)^2 = D(dx) g(dy) + g(0) D(dy), D = g - g(t,0)
+        D = _g1d_minus_g0(t, d)
+        g0 = g[:, :1]
+        reg = (D[:, None, :] * g[:, :, None] + (g0 * D)[:, :, None]) * w[:, None, None]
+        c = 2.0 * math.log(math.pi / h) + 2.0 * _EULER_GAMMA - 4.0 * _CATALAN / math.pi
+        out[~pos] = 2.0 * reg.sum(axis=0) + c
+    return (h * h) * out
+
+
+def _window(n):
+    """Indices of the zero-padded periodic embedding: slot d mod 2n <- |d|,
+    d in [-(n-1), n] (slot n carries the value at n, as in kernel_spectrum)."""
+    return np.concatenate([np.arange(n + 1), np.arange(n - 1, 0, -1)])
+
+
+def kernel_spectrum_slab(n, h):
+    """Slab spectrum in scipy's rfftn layout of the (2n, n, n) grid [z, y, x]:
+    shape (2n, n, n//2 + 1); z zero-padded, x and y periodic (n even)."""
+    if n % 2:
+        raise ValueError("the slab kernel needs an even n")
+    my = np.fft.fftfreq(n, d=1.0 / n)
+    mx = np.arange(n // 2 + 1, dtype=np.float64)
+    m2 = my[:, None] ** 2 + mx[None, :] ** 2
+    uq, inv = np.unique(m2, return_inverse=True)
+    K = slab_kernel_z(n, h, 2.0 * np.pi * np.sqrt(uq) / n)     # (nu, n+1)
+    spec = sfft.rfft(K[:, _window(n)], axis=1, workers=-1).real  # (nu, n+1): kz in [0, n]
+    kz = np.concatenate([np.arange(n + 1), np.arange(n - 1, 0, -1)])
+    return np.ascontiguousarray(spec[inv.reshape(m2.shape)][..., kz].transpose(2, 0, 1))
+
+
+def kernel_spectrum_wire(n, h):
+    """Wire spectrum in scipy's rfftn layout of the (n, 2n, 2n) grid [z, y, x]:
+    shape (n, 2n, n + 1); x and y zero-padded, z periodic (n even)."""
+    if n % 2:
+        raise ValueError("the wire kernel needs an even n")
+    mz = np.abs(np.fft.fftfreq(n, d=1.0 / n))
+    uq, inv = np.unique(mz, return_inverse=True)
+    K2 = wire_kernel_xy(n, h, 2.0 * np.pi * uq / n)            # (nu, n+1, n+1)
+    idx = _window(n)
+    spec = sfft.rfft2(K2[:, idx][:, :, idx], workers=-1).real   # (nu, 2n, n+1)
+    return np.ascontiguousarray(spec[inv])
+
+
 def poisson(rho, Ghat):
-    """V = G * rho.  A spectrum of the padded (2n)^3 grid (kernel_spectrum)
-    gives the aperiodic convolution through the zero-padded FFT (Sec. 2.1.2);
-    one of the n^3 grid (kernel_spectrum_periodic) the periodic solution."""
+    """V = G * rho on the n^3 grid.  The spectrum's shape says which axes are
+    zero-padded to 2n (free: the aperiodic convolution of Sec. 2.1.2) and which
+    are periodic: (2n, 2n, n+1) free (kernel_spectrum), (n, n, n/2+1) periodic,
+    (2n, n, n/2+1) slab, (n, 2n, n+1) wire."""
     n = rho.shape[0]
-    if Ghat.shape[0] == n:
+    shape = (2 * n if Ghat.shape[0] == 2 * n else n,
+             2 * n if Ghat.shape[1] == 2 * n else n,
+             2 * n if Ghat.shape[2] == n + 1 else n)
+    if shape == rho.shape:
         return np.ascontiguousarray(sfft.irfftn(sfft.rfftn(rho, workers=-1) * Ghat, s=rho.shape,
                                                 workers=-1))
-    pad = np.zeros((2 * n,) * 3, dtype=np.float64)
+    pad = np.zeros(shape, dtype=np.float64)
     pad[:n, :n, :n] = rho
-    V = sfft.irfftn(sfft.rfftn(pad, workers=-1) * Ghat, s=(2 * n,) * 3, workers=-1)
+    V = sfft.irfftn(sfft.rfftn(pad, workers=-1) * Ghat, s=shape, workers=-1)
     return np.ascontiguousarray(V[:n, :n, :n])
 
 

@@ -361,3 +361,143 @@ def test_periodic_exchange_invariants():
             V = o.poisson(psi[i] * psi[j], Gp)
             tot += 4.0 * r.h ** 3 * float(np.sum(psi[i] * psi[j] * V))
     assert Ex == pytest.approx(-0.5 * 0.25 * tot, rel=1e-13)
+
+
+# ------------------------------------------------ slab and wire boundary conditions
+# Slab: x, y periodic (cell n h), z free.  Wire: x, y free, z periodic.  The
+# densities below are band-limited on the free axes (sigma >= 2.5 h) and fit
+# the box (sigma <= half-box / 7), so the band-limited kernels must reproduce
+# the continuum potentials to rounding.
+
+def _gauss1(u, s):
+    return np.exp(-u * u / (2 * s * s)) / (s * math.sqrt(2 * math.pi))
+
+
+def test_slab_charged_sheet_potential():
+    # uniform in the plane, Gaussian profile in z (unit charge per area):
+    # V(z) = -2 pi int |z - z'| rho(z') dz' = -2 pi [z erf(z / (s sqrt 2)) + s sqrt(2/pi) e^{-z^2/2s^2}]
+    n, h, s = 48, 0.2, 0.6
+    zz = np.arange(n) * h - (n - 1) * h / 2
+    rho = np.broadcast_to(_gauss1(zz, s)[:, None, None], (n, n, n)).copy()
+    V = o.poisson(rho, o.kernel_spectrum_slab(n, h))
+    ref = -2 * math.pi * (zz * special.erf(zz / (s * math.sqrt(2)))
+                          + s * math.sqrt(2 / math.pi) * np.exp(-zz ** 2 / (2 * s * s)))
+    assert np.max(np.abs(V - ref[:, None, None])) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("mx,my", [(1, 0), (3, 2), (7, 0), (0, 5)])
+def test_slab_plane_wave_times_gaussian(mx, my):
+    # rho = cos(k . r_par) g(z): V = cos(k . r_par) (2 pi / k) int e^{-k|z-z'|} g(z') dz'
+    #     = cos(k . r_par) (pi / k) e^{-z^2/2s^2} [erfcx((k s^2 - z)/(s sqrt 2)) + erfcx((k s^2 + z)/(s sqrt 2))]
+    n, h, s = 48, 0.2, 0.6
+    x = np.arange(n) * h
+    zz = x - (n - 1) * h / 2
+    kx, ky = 2 * math.pi * mx / (n * h), 2 * math.pi * my / (n * h)
+    k = math.hypot(kx, ky)
+    plane = np.cos(ky * x[:, None] + kx * x[None, :])        # [y, x]
+    rho = _gauss1(zz, s)[:, None, None] * plane[None]
+    V = o.poisson(rho, o.kernel_spectrum_slab(n, h))
+    a = (k * s * s - zz) / (s * math.sqrt(2))
+    b = (k * s * s + zz) / (s * math.sqrt(2))
+    Vz = (math.pi / k) * np.exp(-zz ** 2 / (2 * s * s)) * (special.erfcx(a) + special.erfcx(b))
+    ref = Vz[:, None, None] * plane[None]
+    assert np.max(np.abs(V - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("kappa,d", [(0.3, 0), (0.3, 5), (1.7, 2), (2.9, 11)])
+def test_slab_kernel_entries_against_quadpack(kappa, d):
+    # h g(k, d h) = h 4 int_0^{pi/h} cos(q d h) / (k^2 + q^2) dq (QUADPACK's
+    # cosine-weighted rule, not the oracle's t-integral)
+    # (d = 0: the closed form (4 / k) atan(pi / (h k)))
+    n, h = 16, 0.4
+    k = kappa / h
+    if d == 0:
+        val = 4.0 / k * math.atan(math.pi / (h * k))
+    else:
+        val, _ = integrate.quad(lambda q: 4.0 / (k * k + q * q), 0.0, math.pi / h, weight="cos",
+                                wvar=d * h, epsabs=1e-13, epsrel=1e-13)
+    got = o.slab_kernel_z(n, h, [kappa])[0, d]
+    assert got == pytest.approx(h * val, rel=1e-12, abs=1e-14)
+
+
+def test_wire_line_charge_potential():
+    # uniform along z, 2D Gaussian across (unit charge per length):
+    # V(r) = -2 ln r - E1(r^2 / (2 s^2))  (-> -2 ln r far away; gamma - ln(2 s^2) at r = 0)
+    n, h, s = 48, 0.2, 0.6
+    u = np.arange(n) * h - (n // 2) * h
+    r2 = u[:, None] ** 2 + u[None, :] ** 2                     # [y, x]
+    rho2 = np.exp(-r2 / (2 * s * s)) / (2 * math.pi * s * s)
+    V = o.poisson(np.broadcast_to(rho2[None], (n, n, n)).copy(), o.kernel_spectrum_wire(n, h))
+    ref = np.empty_like(r2)
+    nz = r2 > 0
+    ref[nz] = -np.log(r2[nz]) - special.exp1(r2[nz] / (2 * s * s))
+    ref[~nz] = np.euler_gamma - math.log(2 * s * s)
+    assert np.max(np.abs(V - ref[None])) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("mz", [1, 2, 5])
+def test_wire_axial_wave_times_gaussian(mz):
+    # rho = cos(k z) g2(r): V = cos(k z) 2 int_0^inf q J0(q r) e^{-q^2 s^2/2} / (k^2 + q^2) dq,
+    # = cos(k z) e^{k^2 s^2/2} E1(k^2 s^2/2) on the axis
+    n, h, s = 48, 0.2, 0.6
+    x = np.arange(n) * h
+    u = x - (n // 2) * h
+    r2 = u[:, None] ** 2 + u[None, :] ** 2
+    k = 2 * math.pi * mz / (n * h)
+    rho = np.cos(k * x)[:, None, None] * (np.exp(-r2 / (2 * s * s)) / (2 * math.pi * s * s))[None]
+    V = o.poisson(rho, o.kernel_spectrum_wire(n, h))
+    axis = math.exp(k * k * s * s / 2) * special.exp1(k * k * s * s / 2)
+    assert V[0, n // 2, n // 2] == pytest.approx(axis, rel=1e-12)
+    for (iy, ix) in [(n // 2, n // 2 + 3), (n // 2 + 7, n // 2 - 4), (3, 40)]:
+        rr = math.sqrt(r2[iy, ix])
+        val, _ = integrate.quad(lambda q: 2 * q * special.j0(q * rr) * math.exp(-q * q * s * s / 2)
+                                / (k * k + q * q), 0, 15.0 / s, epsabs=1e-14, epsrel=1e-13, limit=400)
+        assert V[0, iy, ix] == pytest.approx(val, rel=1e-11, abs=1e-13)
+
+
+def _mixed_direct_sum(rho, K, per_axes):
+    """V[m] = sum_m' Kr[m - m'] rho[m'] with per-axis differences taken mod n on
+    the periodic axes and as |m - m'| on the free ones (O(n^6), tiny n)."""
+    n = rho.shape[0]
+    idx = np.arange(n)
+    dif = [((idx[:, None] - idx[None, :]) % n) if p else np.abs(idx[:, None] - idx[None, :])
+           for p in per_axes]
+    V = np.empty_like(rho)
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                V[z, y, x] = np.sum(K[dif[0][z][:, None, None], dif[1][y][None, :, None],
+                                      dif[2][x][None, None, :]] * rho)
+    return V
+
+
+def test_slab_and_wire_padded_fft_equal_direct_sums():
+    # the real-space kernels, periodised by an explicit inverse DFT over the
+    # periodic axes, summed directly: pins the zero padding, the window and the
+    # spectrum assembly of kernel_spectrum_slab / _wire
+    n, h = 6, 0.45
+    rng = _rng(21)
+    rho = rng.standard_normal((n, n, n))
+    m = np.fft.fftfreq(n, d=1.0 / n)
+    # slab: Kr[dz][dy][dx] = (1/n^2) sum_{my, mx} e^{2 pi i (my dy + mx dx)/n} K[kappa(my, mx)][dz]
+    kap = 2 * math.pi * np.sqrt(m[:, None] ** 2 + m[None, :] ** 2) / n
+    Kz = o.slab_kernel_z(n, h, kap.ravel()).reshape(n, n, n + 1)      # [my][mx][dz]
+    Kr = np.real(np.fft.ifft2(Kz, axes=(0, 1))).transpose(2, 0, 1)    # [dz][dy][dx]
+    V = o.poisson(rho, o.kernel_spectrum_slab(n, h))
+    assert np.max(np.abs(V - _mixed_direct_sum(rho, Kr, (False, True, True)))) <= 1e-12 * np.max(np.abs(V))
+    # wire: Kr[dz][dy][dx] = (1/n) sum_mz e^{2 pi i mz dz/n} K2[kappa(mz)][dy][dx]
+    K2 = o.wire_kernel_xy(n, h, 2 * math.pi * np.abs(m) / n)          # [mz][dy][dx]
+    Kr = np.real(np.fft.ifft(K2, axis=0))
+    V = o.poisson(rho, o.kernel_spectrum_wire(n, h))
+    assert np.max(np.abs(V - _mixed_direct_sum(rho, Kr, (True, False, False)))) <= 1e-12 * np.max(np.abs(V))
+
+
+def test_slab_and_wire_exchange_invariants():
+    r, psi = _small_case(seed=10, n=8, N=3)
+    for Gm in (o.kernel_spectrum_slab(r.n, r.h), o.kernel_spectrum_wire(r.n, r.h)):
+        Ex, vx, Eij = o.exx(psi, np.full(3, 2.0), 0.25, r.h, Gm)
+        assert np.allclose(Eij, Eij.T, rtol=0, atol=0)
+        assert Ex == pytest.approx(0.5 * 2.0 * r.h ** 3 * float(np.sum(psi * vx)), rel=1e-12)
+        # homogeneity: E_x(c psi) = c^4 E_x
+        E2, _, _ = o.exx(1.3 * psi, np.full(3, 2.0), 0.25, r.h, Gm, want_vx=False)
+        assert E2 == pytest.approx(1.3 ** 4 * Ex, rel=1e-12)
