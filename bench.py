@@ -51,8 +51,9 @@ def args_parse():
                     help="orbital workload of the timed step (default: 64 orbitals on 96^3)")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 16-molecule batched workload (one graph launch)")
-    ap.add_argument("--bc", choices=["free", "periodic"], default="free",
-                    help="boundary conditions: free (zero-padded 2n FFTs) or periodic cell")
+    ap.add_argument("--bc", choices=["free", "periodic", "slab", "wire"], default="free",
+                    help="boundary conditions: free (zero-padded 2n FFTs), periodic cell, slab "
+                         "(x, y periodic, z free) or wire (x, y free, z periodic)")
     ap.add_argument("--norb", type=int, default=0,
                     help="use only the first NORB orbitals (small profiling cases)")
     return ap.parse_args()
@@ -148,25 +149,32 @@ def tile_list(N, T):
     return out
 
 
-def algorithmic_bytes(n, N, T, rs=4, periodic=False):
+def half_lines(n, bc):
+    """Half line lengths (x and y, z) of the transforms: n on a free
+    (zero-padded) axis, n/2 on a periodic one."""
+    return {"free": (n, n), "periodic": (n // 2, n // 2), "slab": (n // 2, n),
+            "wire": (n, n // 2)}[bc]
+
+
+def algorithmic_bytes(n, N, T, rs=4, bc="free"):
     """Minimal HBM bytes of each kernel kind over one exx_apply.
 
-    Transforms of length 2h, h = n (free BC, padded) or n/2 (periodic).  Per
-    pair: fwd_xy writes the y-transformed spectrum X2 ((h+1) n 2h complex);
+    x and y transforms of length 2h, z transforms of length 2hz (half_lines).
+    Per pair: fwd_xy writes the y-transformed spectrum X2 ((h+1) n 2h complex);
     zconv reads it and writes X3 in place; inv_yx reads X3 and writes V (n^3);
     accum reads V.  Per tile: fwd_xy and accum read the tile's orbitals once,
     accum reads and writes their FP64 accumulators once; zconv reads the
-    kernel table ((h+1) (2h)^2) once per launch.
+    kernel table ((h+1) 2hz 2h) once per launch.
     """
     cs = 2 * rs
-    hl = n // 2 if periodic else n
+    hl, hz = half_lines(n, bc)
     spec = (hl + 1) * n * 2 * hl * cs
     n3 = n ** 3
     tot = {"fwd_xy": 0, "zconv": 0, "inv_yx": 0, "accum": 0}
     for npair, ti, tj, diag in tile_list(N, T):
         orbs = ti if diag else ti + tj
         tot["fwd_xy"] += orbs * n3 * rs + npair * spec
-        tot["zconv"] += 2 * npair * spec + (hl + 1) * (2 * hl) ** 2 * rs
+        tot["zconv"] += 2 * npair * spec + (hl + 1) * (2 * hz) * (2 * hl) * rs
         tot["inv_yx"] += npair * spec + npair * n3 * rs
         tot["accum"] += npair * n3 * rs + orbs * n3 * rs + 2 * orbs * n3 * 8
     return tot
@@ -187,13 +195,15 @@ def committed_traffic(kernel):
 
 
 # ------------------------------------------------------------ CPU oracle
-def cpu_oracle_rate(psi, r, npairs, seed=0, periodic=False):
+def cpu_oracle_rate(psi, r, npairs, seed=0, bc="free"):
     """Time the FP64 oracle on a seeded sample of the workload's pair solves
     (co-density, FFT Poisson solve, E_ij, both V psi products)."""
     import numpy as np
     from oracle import exx_oracle as o
-    Gh = (o.kernel_spectrum_periodic(r.n, r.h) if periodic
-          else o.kernel_spectrum(o.kernel_real_space(r.n, r.h)))
+    Gh = {"periodic": lambda: o.kernel_spectrum_periodic(r.n, r.h),
+          "slab": lambda: o.kernel_spectrum_slab(r.n, r.h),
+          "wire": lambda: o.kernel_spectrum_wire(r.n, r.h),
+          "free": lambda: o.kernel_spectrum(o.kernel_real_space(r.n, r.h))}[bc]()
     rng = np.random.default_rng(seed)
     pairs = o.pair_list(r.norb)
     pick = [pairs[k] for k in rng.choice(len(pairs), size=npairs, replace=False)]
@@ -318,8 +328,8 @@ def run_ours(a):
     N, n = r.norb, r.n
     P = N * (N + 1) // 2
     occ = np.full(N, r.occupation)
-    per = a.bc == "periodic"
-    kern = "periodic" if per else "sinc"
+    per = a.bc != "free"
+    kern = "sinc" if a.bc == "free" else a.bc
     plan = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp32", kernel=kern)
     info = plan.info()
     out = torch.empty(psi.shape, dtype=torch.float32, device=dev)
@@ -360,7 +370,7 @@ def run_ours(a):
     ms_step = ms / a.steps
 
     # roofline of the dominant kernel
-    alg = algorithmic_bytes(n, N, info["tile"], periodic=per)
+    alg = algorithmic_bytes(n, N, info["tile"], bc=a.bc)
     dom = max(alg, key=lambda k: prof[k][0])
     kms, kcnt = prof[dom]
     per_launch_bytes = alg[dom] / (kcnt / a.steps)
@@ -376,7 +386,7 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": a.workload, "bc": a.bc, "norb": N, "n": n,
-                       "fft_grid": n if per else 2 * n, "h": r.h,
+                       "fft_grid": [2 * hh for hh in half_lines(n, a.bc)], "h": r.h,
                        "pairs": P, "tile": info["tile"], "precision": "fp32 ffts, fp64 reductions",
                        "l2": "inputs larger than L2 (psi 226 MB; pair-tile spectra 0.2-0.9 GB)",
                        "parallelism": f"replicas x{world}"},
@@ -473,7 +483,7 @@ def run_ours(a):
         if big:
             psi_np = psi.double().cpu().numpy()
         a.cpu_sample = sample
-        rate, dt = cpu_oracle_rate(psi_np, r, a.cpu_sample, periodic=per)
+        rate, dt = cpu_oracle_rate(psi_np, r, a.cpu_sample, bc=a.bc)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle", "seconds": dt,
                                 "sample": f"{a.cpu_sample} seeded pair solves (of {P}) of the same "

@@ -71,11 +71,24 @@ typedef enum {
                              screened hybrids (HSE-type; Sec. 3 notes that only
                              the Poisson filter changes); needs omega > 0 and
                              exx_plan_create_desc                                 */
-  EXX_KERNEL_PERIODIC = 3 /* periodic boundary conditions on the n^3 cell of side
+  EXX_KERNEL_PERIODIC = 3, /* periodic boundary conditions on the n^3 cell of side
                              n h (the paper's own runs, Sec. 3, are periodic):
                              V_hat = 4 pi rho_hat / |k|^2 with k = 0 removed, no
                              padding; n even, n in {8,12,16,24,32,48,64,96,128,
                              192} (FP64 up to 128)                                */
+  EXX_KERNEL_SLAB = 4,    /* slab ("surface") boundary conditions (Sec. 2.1.2:
+                             other boundary conditions change only the Green's
+                             function): x and y periodic with the cell n h, z
+                             free (zero-padded to 2n); per in-plane frequency k
+                             the band-limited 1D kernel of d2/dz2 - k^2, at k = 0
+                             the one whose potential of band-limited densities is
+                             -2 pi int |z - z'| rho dz'; n in {8,16,32,48,64,96} */
+  EXX_KERNEL_WIRE = 5     /* wire boundary conditions: x and y free (zero-padded),
+                             z periodic with the cell n h; per axial frequency k
+                             the band-limited 2D kernel of lap_2 - k^2, at k = 0
+                             the one whose potential of band-limited densities is
+                             -2 int ln|r - r'| rho d2r' (r in bohr);
+                             n in {8,16,32,48,64,96}                              */
 } exx_kernel_t;
 
 /* Plan flags (bitwise or). */
@@ -321,6 +334,10 @@ exx_status_t exx_plan_destroy(exx_plan_t plan);
  * EXX_KERNEL_ERFC only.  out_host holds (n+1)^3 doubles, index
  * (kz*(n+1) + ky)*(n+1) + kx.  EXX_KERNEL_PERIODIC (n even): 4 pi / |k|^2,
  * k = 2 pi m / (n h), m in [0, n/2]^3, 0 at m = 0; (n/2+1)^3 doubles.
+ * EXX_KERNEL_SLAB (n even): kz in [0, n] (padded axis), kx, ky in [0, n/2];
+ * (n+1)(n/2+1)^2 doubles, index (kz*(n/2+1) + ky)*(n/2+1) + kx.
+ * EXX_KERNEL_WIRE (n even): kz in [0, n/2] (periodic axis), kx, ky in [0, n];
+ * (n/2+1)(n+1)^2 doubles, index (kz*(n+1) + ky)*(n+1) + kx.
  * Needs no GPU.
  */
 exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double omega, double* out_host);

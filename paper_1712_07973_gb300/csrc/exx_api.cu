@@ -33,6 +33,9 @@ namespace exx {
 
 // periodic boundary conditions: half grids (grid = 2 N)
 #define EXX_PSIZES(X) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96)
+// slab boundary conditions: half grids (grid = 2 N); wire: grids
+#define EXX_SSIZES(X) X(4) X(8) X(16) X(24) X(32) X(48)
+#define EXX_WSIZES(X) X(8) X(16) X(32) X(48) X(64) X(96)
 
 #define EXX_DECL(N) const Ops* ops_f32_##N(); const Ops* ops_f64_##N();
 EXX_SIZES(EXX_DECL)
@@ -40,6 +43,38 @@ EXX_SIZES(EXX_DECL)
 #define EXX_DECL(N) const Ops* ops_pf32_##N(); const Ops* ops_pf64_##N();
 EXX_PSIZES(EXX_DECL)
 #undef EXX_DECL
+#define EXX_DECL(N) const Ops* ops_sf32_##N(); const Ops* ops_sf64_##N();
+EXX_SSIZES(EXX_DECL)
+#undef EXX_DECL
+#define EXX_DECL(N) const Ops* ops_wf32_##N(); const Ops* ops_wf64_##N();
+EXX_WSIZES(EXX_DECL)
+#undef EXX_DECL
+
+// slab grid n = 2 N
+static const Ops* lookup_ops_slab(int prec, int n) {
+  if (n % 2 != 0) return nullptr;
+  switch (n / 2) {
+#define EXX_CASE(N) \
+  case N:           \
+    return prec == EXX_FP64 ? ops_sf64_##N() : ops_sf32_##N();
+    EXX_SSIZES(EXX_CASE)
+#undef EXX_CASE
+    default:
+      return nullptr;
+  }
+}
+
+static const Ops* lookup_ops_wire(int prec, int n) {
+  switch (n) {
+#define EXX_CASE(N) \
+  case N:           \
+    return prec == EXX_FP64 ? ops_wf64_##N() : ops_wf32_##N();
+    EXX_WSIZES(EXX_CASE)
+#undef EXX_CASE
+    default:
+      return nullptr;
+  }
+}
 
 // periodic grid n = 2 N
 static const Ops* lookup_ops_periodic(int prec, int n) {
@@ -201,6 +236,7 @@ struct exx_plan_s {
   // device memory
   void* Gs = nullptr;
   void* tw = nullptr;
+  void* twz = nullptr;  // twiddles of the z transform where its length differs
   double* d_occ = nullptr;
   int4* d_pairs = nullptr;
   double* epart = nullptr;
@@ -238,8 +274,8 @@ exx_status_t cuda_fail(exx_plan_t p, cudaError_t e) {
   } while (0)
 
 void free_plan(exx_plan_t p) {
-  void* ptrs[] = {p->Gs, p->tw,   p->d_occ, p->d_pairs, p->epart, p->Epair, p->X2,
-                  p->V,  p->vacc, p->E_dev, p->d_err,   p->h_psi, p->h_vx};
+  void* ptrs[] = {p->Gs,   p->tw,    p->twz,  p->d_occ, p->d_pairs, p->epart, p->Epair,
+                  p->X2,   p->V,     p->vacc, p->E_dev, p->d_err,   p->h_psi, p->h_vx};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (int k = 0; k < EXX_NKINDS; ++k)
@@ -330,8 +366,7 @@ const char* exx_version(void) { return "exx-gb300 0.1 (sm_103a)"; }
 
 exx_status_t exx_kernel_spectrum(int n, double h, int kernel, double omega, double* out_host) {
   if (n < 1 || !(h > 0.0) || out_host == nullptr) return EXX_ERR_INVALID_ARG;
-  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC &&
-      kernel != EXX_KERNEL_PERIODIC)
+  if (kernel < EXX_KERNEL_SINC || kernel > EXX_KERNEL_WIRE)
     return EXX_ERR_INVALID_ARG;
   return exx_host::kernel_spectrum_octant(n, h, kernel, omega, out_host) ? EXX_OK
                                                                           : EXX_ERR_INVALID_ARG;
@@ -372,8 +407,7 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   if (!(h[0] > 0.0) || !(h[1] > 0.0) || !(h[2] > 0.0) || !std::isfinite(alpha))
     return EXX_ERR_INVALID_ARG;
   if (precision != EXX_FP64 && precision != EXX_FP32) return EXX_ERR_INVALID_ARG;
-  if (kernel != EXX_KERNEL_SINC && kernel != EXX_KERNEL_HOCKNEY && kernel != EXX_KERNEL_ERFC &&
-      kernel != EXX_KERNEL_PERIODIC)
+  if (kernel < EXX_KERNEL_SINC || kernel > EXX_KERNEL_WIRE)
     return EXX_ERR_INVALID_ARG;
   if (flags & ~((unsigned)EXX_FLAG_VX_FP64 | EXX_FLAG_TILE(15))) return EXX_ERR_INVALID_ARG;
   const int tile_req = (int)((flags >> 8) & 15u);
@@ -384,11 +418,14 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
     return EXX_ERR_NOT_SUPPORTED;
   const int n = grid[0];
   const Ops* ops = kernel == EXX_KERNEL_PERIODIC ? lookup_ops_periodic(precision, n)
+                   : kernel == EXX_KERNEL_SLAB  ? lookup_ops_slab(precision, n)
+                   : kernel == EXX_KERNEL_WIRE  ? lookup_ops_wire(precision, n)
                    : split_l1(2 * n) == 0       ? nullptr
                                                 : lookup_ops(precision, n);
   if (ops == nullptr || !ops->supported) return EXX_ERR_NOT_SUPPORTED;
-  // transforms of length 2 nh: nh = n (free BC, padded) or n / 2 (periodic)
-  const int nh = ops->n;
+  // x and y transforms of length 2 nh, z transforms of length 2 nz: n (free
+  // axis, padded) or n / 2 (periodic axis)
+  const int nh = ops->n, nz = ops->nz;
 
   exx_plan_t p = new exx_plan_s();
   p->n = n;
@@ -422,37 +459,41 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   }
   p->mine.assign(p->tiles.size(), 1);
 
-  // kernel spectrum (FP64, host, one octant k <= nh), scaled by the
-  // inverse-FFT normalisation
+  // kernel spectrum (FP64, host, one octant kz <= nz, kx, ky <= nh), scaled
+  // by the inverse-FFT normalisation
   const size_t m = (size_t)nh + 1;
-  std::vector<double> Gh(m * m * m);
+  std::vector<double> Gh(((size_t)nz + 1) * m * m);
   if (!exx_host::kernel_spectrum_octant(n, p->h, kernel, p->omega, Gh.data())) {
     delete p;
     return EXX_ERR_INVALID_ARG;
   }
-  const double L = 2.0 * nh;
-  const double scale = 1.0 / (L * L * L);
+  const double L = 2.0 * nh, LZ = 2.0 * nz;
+  const double scale = 1.0 / (L * L * LZ);
   const size_t rs = precision == EXX_FP64 ? sizeof(double) : sizeof(float);
   const size_t cs = 2 * rs;
-  // kernel table (scaled by 1/(2n)^3; for FP32 with the forward transforms'
+  // kernel table (scaled by 1/(L^2 LZ); for FP32 with the forward transforms'
   // gains divided out) and twiddle tables (exx_ops.cuh)
-  std::vector<unsigned char> gbuf(exx::kernel_table_bytes(nh, rs, ops->table_fold_y)),
-      twbuf(exx::twiddle_count(nh) * cs);
-  std::vector<double> gx, gz;
+  std::vector<unsigned char> gbuf(exx::kernel_table_bytes(nh, nz, rs, ops->table_fold_y)),
+      twbuf(exx::twiddle_count(nh) * cs), twzbuf(nz != nh ? exx::twiddle_count(nz) * cs : 0);
+  std::vector<double> gx, gy, gz;
   if (ops->gains) {
     gx.resize(m);
-    gz.resize(2 * (size_t)nh);
-    ops->gains(gx.data(), gz.data());
+    gy.resize(2 * (size_t)nh);
+    gz.resize(2 * (size_t)nz);
+    ops->gains(gx.data(), gy.data(), gz.data());
   }
   if (precision == EXX_FP64) {
-    exx::build_kernel_table<double>(nh, ops->table_fold_y, Gh.data(), scale, nullptr, nullptr,
-                                    gbuf.data());
+    exx::build_kernel_table<double>(nh, nz, ops->table_fold_y, Gh.data(), scale, nullptr, nullptr,
+                                    nullptr, gbuf.data());
     exx::build_twiddles(nh, reinterpret_cast<double*>(twbuf.data()));
+    if (nz != nh) exx::build_twiddles(nz, reinterpret_cast<double*>(twzbuf.data()));
   } else {
-    exx::build_kernel_table<float>(nh, ops->table_fold_y, Gh.data(), scale,
-                                   gx.empty() ? nullptr : gx.data(), gz.empty() ? nullptr : gz.data(),
-                                   gbuf.data());
+    const bool g = !gx.empty();
+    exx::build_kernel_table<float>(nh, nz, ops->table_fold_y, Gh.data(), scale,
+                                   g ? gx.data() : nullptr, g ? gy.data() : nullptr,
+                                   g ? gz.data() : nullptr, gbuf.data());
     exx::build_twiddles(nh, reinterpret_cast<float*>(twbuf.data()));
+    if (nz != nh) exx::build_twiddles(nz, reinterpret_cast<float*>(twzbuf.data()));
   }
 
   const long long n3 = (long long)n * n * n;
@@ -466,6 +507,9 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   }
   EXX_ALLOC(p->Gs, gbuf.size());
   EXX_ALLOC(p->tw, twbuf.size());
+  if (!twzbuf.empty()) {
+    EXX_ALLOC(p->twz, twzbuf.size());
+  }
   EXX_ALLOC(p->d_occ, norb * sizeof(double));
   EXX_ALLOC(p->d_pairs, pairs.size() * sizeof(int4));
   EXX_ALLOC(p->epart, (size_t)p->maxpairs * nper * sizeof(double));
@@ -481,6 +525,8 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
 
   cudaError_t e = cudaMemcpyAsync(p->Gs, gbuf.data(), gbuf.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->tw, twbuf.data(), twbuf.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && p->twz)
+    e = cudaMemcpyAsync(p->twz, twzbuf.data(), twzbuf.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_occ, p->occ.data(), norb * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -498,7 +544,7 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
     }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&p->gmap, p->Gs, nh))
+  if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&p->gmap, p->Gs, nh, nz))
     e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = ops->setup();
   if (e != cudaSuccess) {
@@ -558,7 +604,8 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
     }
     {
       ProfScope ps(p, K_ZCONV, st);
-      p->ops->zconv(p->X2, p->Gs, p->tw, &p->gmap, p->epart, p->d_err, t.count, !apply, st);
+      p->ops->zconv(p->X2, p->Gs, p->twz ? p->twz : p->tw, &p->gmap, p->epart, p->d_err, t.count,
+                    !apply, st);
     }
     {
       ProfScope ps(p, K_PAIRE, st);

@@ -422,10 +422,11 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
       return EXX_ERR_INVALID_ARG;
     }
     const double L = 2.0 * g.n, scale = 1.0 / (L * L * L);
-    std::vector<double> gx(m), gz(2 * (size_t)g.n);
-    g.ops->gains(gx.data(), gz.data());
-    std::vector<unsigned char> gf(exx::kernel_table_bytes(g.n, sizeof(float), g.ops->table_fold_y));
-    exx::build_kernel_table<float>(g.n, g.ops->table_fold_y, Gh.data(), scale, gx.data(), gz.data(), gf.data());
+    std::vector<double> gx(m), gy(2 * (size_t)g.n), gz(2 * (size_t)g.n);
+    g.ops->gains(gx.data(), gy.data(), gz.data());
+    std::vector<unsigned char> gf(exx::kernel_table_bytes(g.n, g.n, sizeof(float), g.ops->table_fold_y));
+    exx::build_kernel_table<float>(g.n, g.n, g.ops->table_fold_y, Gh.data(), scale, gx.data(),
+                                   gy.data(), gz.data(), gf.data());
     std::vector<float> tw(2 * exx::twiddle_count(g.n));
     exx::build_twiddles(g.n, tw.data());
     if (!balloc(b, &g.Gs, gf.size()) || !balloc(b, &g.tw, tw.size() * sizeof(float))) {
@@ -436,7 +437,7 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
     up(g.Gs, gf.data(), gf.size());
     up(g.tw, tw.data(), tw.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host buffers die at scope end
-    if (e == cudaSuccess && g.ops->stage_table && !exx::make_ktab_map(&g.gmap, g.Gs, g.n))
+    if (e == cudaSuccess && g.ops->stage_table && !exx::make_ktab_map(&g.gmap, g.Gs, g.n, g.n))
       e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = g.ops->setup();
   }

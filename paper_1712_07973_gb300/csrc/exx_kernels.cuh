@@ -377,14 +377,22 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 // global memory in the second pass.  A wait that runs out sets err[0];
 // err[1] != 0 (a test hook set by the host) skips issuing the copy, so that
 // the bounded wait runs out on purpose.
-template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool PER, bool ENERGY_ONLY>
+// (N, PER) describe the x and y axes (kx <= N, ky < 2N), (NZ, PERZ) the z
+// transform (length 2NZ, tw_g its twiddles); they differ for the mixed
+// boundary conditions: slab (x, y periodic, z free) and wire (x, y free,
+// z periodic).
+template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool PER, bool ENERGY_ONLY,
+          int NZ = N, bool PERZ = PER>
 __global__ void __launch_bounds__(32 * NW, MINB)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
         double* __restrict__ epart, const __grid_constant__ CUtensorMap gmap, int* __restrict__ err) {
   using C = cplx<R>;
-  constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
-  constexpr int W = L < 32 ? L : 32;
+  constexpr int LY = 2 * N;  // ky extent: the row stride of X and of the kernel table
+  constexpr int L = 2 * NZ, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
+  constexpr int W = LY < 32 ? LY : 32;
   constexpr int M = N + 1;
+  static_assert((PER ? 2 * N : N) == (PERZ ? 2 * NZ : NZ), "one grid size on all axes");
+  static_assert(!FOLDY || (NZ == N && PERZ == PER), "folded tables are cubic");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);  // w^k [L]
   C* buf = tw + L;                         // [L slots][W]
@@ -399,7 +407,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int yb = blockIdx.x, kx = blockIdx.y, p = blockIdx.z;
   const int ky = yb * W + lane;
-  const bool valid = lane < W && ky < L;
+  const bool valid = lane < W && ky < LY;
   if constexpr (STAGE) {
     static_assert(sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 && L <= 256, "TMA box");
     if (tid == 0) {  // out-of-range ky of a partial last block read as zero
@@ -416,8 +424,8 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
     }
   }
   for (int t = tid; t < L; t += 32 * NW) tw[t] = tw_g[t];
-  constexpr int GR = FOLDY ? N + 1 : L;  // table row length
-  const int kyt = FOLDY ? (ky <= N ? ky : L - ky) : ky;
+  constexpr int GR = FOLDY ? N + 1 : LY;  // table row length
+  const int kyt = FOLDY ? (ky <= N ? ky : LY - ky) : ky;
   const R* __restrict__ Gk = Gs + (long long)kx * L * GR + (valid ? kyt : 0);
   double cyl = 1.0;
   if constexpr (FOLDY) {
@@ -426,9 +434,9 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
       cyl = reinterpret_cast<const double*>(reinterpret_cast<const unsigned char*>(Gs) +
                                             ktab_cy_offset(N, sizeof(R)))[ky];
   }
-  constexpr int G = PER ? 2 * N : N;  // z planes stored (grid points per axis)
-  constexpr int NIN = PER ? L1 : H1;   // nonzero inputs / kept outputs per DFT_L1
-  C* col = X + (((long long)p * M + kx) * G) * L + (valid ? ky : 0);
+  constexpr int G = PERZ ? 2 * NZ : NZ;  // z planes stored (grid points per axis)
+  constexpr int NIN = PERZ ? L1 : H1;    // nonzero inputs / kept outputs per DFT_L1
+  C* col = X + (((long long)p * M + kx) * G) * LY + (valid ? ky : 0);
   __syncthreads();
 
   // forward, pass 1
@@ -436,8 +444,8 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
     C v[L1];
 #pragma unroll
     for (int n1 = 0; n1 < NIN; ++n1)
-      v[n1] = valid ? col[(long long)(L2 * n1 + n2) * L] : mkc<C>(R(0), R(0));
-    dft_fwd_in<L1, PER>(v);
+      v[n1] = valid ? col[(long long)(L2 * n1 + n2) * LY] : mkc<C>(R(0), R(0));
+    dft_fwd_in<L1, PERZ>(v);
     if (lane < W) {
       buf[(n2 * L1) * W + lane] = v[0];
 #pragma unroll
@@ -495,10 +503,10 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 #pragma unroll
       for (int k1 = 0; k1 < L1; ++k1)
         v[k1] = lane < W ? buf[(m2 * L1 + k1) * W + lane] : mkc<C>(R(0), R(0));
-      dft_inv_out<L1, PER>(v);
+      dft_inv_out<L1, PERZ>(v);
       if (valid) {
 #pragma unroll
-        for (int m1 = 0; m1 < NIN; ++m1) col[(long long)(L2 * m1 + m2) * L] = v[m1];
+        for (int m1 = 0; m1 < NIN; ++m1) col[(long long)(L2 * m1 + m2) * LY] = v[m1];
       }
     }
   }
@@ -743,20 +751,20 @@ __device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
   }
 }
 
+// Products and accumulation of one tile at the VEC mesh points from r.
 // MODE 0: any tile; MODE 1: full off-diagonal tile (ti = tj = TM); MODE 2:
 // full diagonal tile.  The full modes make every loop bound and branch a
 // compile-time constant, so that all loads of a J step can be issued at once
 // (with the register budget of two CTAs per SM: 4.9 -> 3.8 ms per exx_apply
 // at n = 96, 64 orbitals).
 template <typename R, int TM, int VEC, int MODE>
-__global__ void __launch_bounds__(256, (sizeof(R) == 4 && MODE == 0) ? 3 : 2)
-k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__ vx,
-        const double* __restrict__ occ, int i0, int ti_, int j0, int tj_, int diag_, double c,
-        long long n3) {
+__device__ __forceinline__ void accum_tile(const R* __restrict__ psi, const R* __restrict__ V,
+                                           double* __restrict__ vx,
+                                           const double* __restrict__ occ, int i0, int ti_,
+                                           int j0, int tj_, int diag_, double c, long long n3,
+                                           long long r) {
   const int ti = MODE ? TM : ti_, tj = MODE ? TM : tj_;
   const bool diag = MODE == 2 ? true : MODE == 1 ? false : diag_ != 0;
-  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
-  if (r >= n3) return;
   R fi[TM];
 #pragma unroll
   for (int a = 0; a < TM; ++a) fi[a] = a < ti ? (R)occ[i0 + a] : R(0);
@@ -805,6 +813,16 @@ k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__
     if (a < ti) vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, c, ai[a]);
 }
 
+template <typename R, int TM, int VEC, int MODE>
+__global__ void __launch_bounds__(256, (sizeof(R) == 4 && MODE == 0) ? 3 : 2)
+k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__ vx,
+        const double* __restrict__ occ, int i0, int ti, int j0, int tj, int diag, double c,
+        long long n3) {
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
+  if (r >= n3) return;
+  accum_tile<R, TM, VEC, MODE>(psi, V, vx, occ, i0, ti, j0, tj, diag, c, n3, r);
+}
+
 // Tile descriptor of a batched wave (tiles of different molecules, or of
 // disjoint orbital blocks, so that no two touch the same accumulator).
 struct TileDesc {
@@ -815,8 +833,10 @@ struct TileDesc {
   double c;   // -alpha of the molecule
 };
 
+// One tile per blockIdx.y; full tiles take the specialised bodies (the branch
+// is uniform over a block).
 template <typename R, int TM, int VEC>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(256, 2)
 k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
               double* const* __restrict__ vx_tab, const double* __restrict__ occ,
               const TileDesc* __restrict__ tiles, long long n3) {
@@ -827,53 +847,14 @@ k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
   double* __restrict__ vx = vx_tab[t.mol];
   const double* __restrict__ oc = occ + t.occ_off;
   const R* __restrict__ Vt = V + (long long)t.voff * n3;
-  const int ti = t.ti, tj = t.tj, i0 = t.i0, j0 = t.j0;
-  const bool diag = t.diag != 0;
-  R fi[TM];
-#pragma unroll
-  for (int a = 0; a < TM; ++a) fi[a] = a < ti ? (R)oc[i0 + a] : R(0);
-  R pi[TM][VEC], ai[TM][VEC];
-#pragma unroll
-  for (int a = 0; a < TM; ++a) {
-    if (a < ti) vload<R, VEC>(psi + (long long)(i0 + a) * n3 + r, pi[a]);
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) ai[a][e] = R(0);
+  if (t.ti == TM && t.tj == TM) {
+    if (t.diag)
+      accum_tile<R, TM, VEC, 2>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 1, t.c, n3, r);
+    else
+      accum_tile<R, TM, VEC, 1>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 0, t.c, n3, r);
+  } else {
+    accum_tile<R, TM, VEC, 0>(psi, Vt, vx, oc, t.i0, t.ti, t.j0, t.tj, t.diag, t.c, n3, r);
   }
-#pragma unroll
-  for (int b = 0; b < TM; ++b) {
-    if (b >= tj) break;
-    const R fb = (R)oc[j0 + b];
-    R pb[VEC], aj[VEC];
-    if (diag) {
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) pb[e] = pi[b][e];
-    } else {
-      vload<R, VEC>(psi + (long long)(j0 + b) * n3 + r, pb);
-    }
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) aj[e] = R(0);
-#pragma unroll
-    for (int a = 0; a < TM; ++a) {
-      if (a >= ti || (diag && a > b)) continue;
-      const int slot = diag ? a * tj - (a * (a - 1)) / 2 + (b - a) : a * tj + b;
-      R v[VEC];
-      vload<R, VEC>(Vt + (long long)slot * n3 + r, v);
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) {
-        ai[a][e] += fb * v[e] * pb[e];
-        if (!(diag && a == b)) aj[e] += fi[a] * v[e] * pi[a][e];
-      }
-    }
-    if (diag) {
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) ai[b][e] += aj[e];
-    } else {
-      vacc<R, VEC>(vx + (long long)(j0 + b) * n3 + r, t.c, aj);
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < TM; ++a)
-    if (a < ti) vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, t.c, ai[a]);
 }
 
 }  // namespace exx

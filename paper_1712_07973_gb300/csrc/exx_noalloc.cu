@@ -33,7 +33,7 @@ const Ops* find_ops(int prec, int n);
 
 constexpr int kNoallocMaxN = EXX_NOALLOC_MAX_N;
 constexpr size_t kSpecElems = (size_t)(kNoallocMaxN + 1) * kNoallocMaxN * 2 * kNoallocMaxN;
-// kernel table (exx::kernel_table_bytes(n, 4, false) / 4 floats for n <= max;
+// kernel table (exx::kernel_table_bytes(n, n, 4, false) / 4 floats for n <= max;
 // n <= 96 never uses the folded layout)
 constexpr size_t kKernElems = (size_t)(kNoallocMaxN + 1) * 2 * kNoallocMaxN * 2 * kNoallocMaxN;
 constexpr int kTwElems = 7 * kNoallocMaxN;  // exx::twiddle_count(n) for n <= max
@@ -112,17 +112,18 @@ exx_status_t load_tables(DeviceScratch& d, const exx::Ops* ops, int n, double h,
   if (!exx_host::kernel_spectrum_octant(n, h, kind, 0.0, G.data())) return EXX_ERR_INVALID_ARG;
   const double L = 2.0 * n;
   const double scale = 1.0 / (L * L * L);
-  std::vector<double> gx(m), gz(2 * (size_t)n);
-  ops->gains(gx.data(), gz.data());
-  std::vector<unsigned char> Gt(exx::kernel_table_bytes(n, sizeof(float), ops->table_fold_y));
-  exx::build_kernel_table<float>(n, ops->table_fold_y, G.data(), scale, gx.data(), gz.data(), Gt.data());
+  std::vector<double> gx(m), gy(2 * (size_t)n), gz(2 * (size_t)n);
+  ops->gains(gx.data(), gy.data(), gz.data());
+  std::vector<unsigned char> Gt(exx::kernel_table_bytes(n, n, sizeof(float), ops->table_fold_y));
+  exx::build_kernel_table<float>(n, n, ops->table_fold_y, G.data(), scale, gx.data(), gy.data(),
+                                 gz.data(), Gt.data());
   std::vector<float2> tw(exx::twiddle_count(n));
   exx::build_twiddles(n, reinterpret_cast<float*>(tw.data()));
   cudaError_t e = cudaMemcpyAsync(d.kern, Gt.data(), Gt.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&d.gmap, d.kern, n))
+  if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&d.gmap, d.kern, n, n))
     e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = ops->setup();
   if (e != cudaSuccess) {

@@ -15,17 +15,20 @@
 namespace exx {
 
 struct Ops {
-  int n = 0;         // half the line length of the transforms (line 2n)
+  int n = 0;         // half the line length of the x and y transforms (line 2n)
+  int nz = 0;        // half the line length of the z transform (= n unless mixed)
   int grid = 0;      // grid points per axis: n (free BC) or 2n (periodic)
-  bool periodic = false;
+  bool periodic = false;    // x and y periodic
+  bool periodic_z = false;  // z periodic
   bool supported = false;
   int nyb = 0;             // zconv column blocks per kx plane
   int nt_a = 0, nt_c = 0;  // threads per CTA of fwd_xy / inv_yx
   int nw_b = 0;            // warps per CTA of zconv
   size_t smem_a = 0, smem_b = 0, smem_c = 0;
   cudaError_t (*setup)() = nullptr;
-  // energy gains of the FP32 forward transforms (null for FP64): gx[n+1], gz[2n]
-  void (*gains)(double* gx, double* gz) = nullptr;
+  // energy gains of the FP32 forward transforms (null for FP64): gx[n+1],
+  // gy[2n], gz[2nz]
+  void (*gains)(double* gx, double* gy, double* gz) = nullptr;
   bool table_fold_y = false;  // kernel-table layout (build_kernel_table)
   // psi_tab (device array of orbital-array pointers, indexed by the pair's
   // molecule slot) may be null, in which case every pair reads psi
@@ -83,10 +86,10 @@ constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_
 }
 
 // TMA descriptor of an FP32 zconv kernel table Gt[kx][kz][ky] (unfolded layout,
-// kx <= n, kz, ky < 2n): 3-D, box of min(2n, 32) ky by 2n kz by one kx, no
-// swizzle, out-of-range elements read as zero.  The driver's encoder is
+// kx <= n, kz < 2nz, ky < 2n): 3-D, box of min(2n, 32) ky by 2nz kz by one kx,
+// no swizzle, out-of-range elements read as zero.  The driver's encoder is
 // reached through the runtime (no link against the driver library).
-inline bool make_ktab_map(CUtensorMap* map, const void* table, int n) {
+inline bool make_ktab_map(CUtensorMap* map, const void* table, int n, int nz) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (encode == nullptr) {
     void* fn = nullptr;
@@ -97,10 +100,10 @@ inline bool make_ktab_map(CUtensorMap* map, const void* table, int n) {
       return false;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t L = 2 * (cuuint64_t)n;
-  const cuuint64_t dims[3] = {L, L, (cuuint64_t)n + 1};
-  const cuuint64_t strides[2] = {L * sizeof(float), L * L * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)(L < 32 ? L : 32), (cuuint32_t)L, 1};
+  const cuuint64_t L = 2 * (cuuint64_t)n, LZ = 2 * (cuuint64_t)nz;
+  const cuuint64_t dims[3] = {L, LZ, (cuuint64_t)n + 1};
+  const cuuint64_t strides[2] = {L * sizeof(float), L * LZ * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)(L < 32 ? L : 32), (cuuint32_t)LZ, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(table), dims, strides,
                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -165,41 +168,48 @@ template <typename R> void build_twiddles(int n, R* out) {
 }
 
 // Kernel table of zconv (layout in exx_kernels.cuh) from the octant
-// Ghat[kx][kz][ky], k <= n: scale * Ghat / (gx[kx] gz[ky] gz[kz]), or with
-// fold_y the ky-folded rows without gz[ky] followed by 1 / gz[ky].  gx, gz are
-// the energy gains |d|^2 of the FP32 forward transforms (exx_gain.cuh; the y
-// and z passes share gz), null for FP64.
-inline size_t kernel_table_bytes(int n, size_t real_size, bool fold_y) {
+// Ghat[kz][ky][kx], kz <= nz, kx, ky <= n: scale * Ghat / (gx[kx] gy[ky] gz[kz]),
+// or with fold_y (nz = n only) the ky-folded rows without gy[ky] followed by
+// 1 / gy[ky].  gx, gy, gz are the energy gains |d|^2 of the FP32 forward
+// transforms (exx_gain.cuh), null for FP64.
+inline size_t kernel_table_bytes(int n, int nz, size_t real_size, bool fold_y) {
   if (fold_y) return ktab_cy_offset(n, real_size) + 2 * (size_t)n * sizeof(double);
-  return (size_t)(n + 1) * (2 * (size_t)n) * (2 * (size_t)n) * real_size;
+  return (size_t)(n + 1) * (2 * (size_t)nz) * (2 * (size_t)n) * real_size;
 }
 template <typename R>
-void build_kernel_table(int n, bool fold_y, const double* octant, double scale, const double* gx,
-                        const double* gz, unsigned char* out) {
-  const size_t m = (size_t)n + 1, L = 2 * (size_t)n, row = fold_y ? m : L;
+void build_kernel_table(int n, int nz, bool fold_y, const double* octant, double scale,
+                        const double* gx, const double* gy, const double* gz, unsigned char* out) {
+  const size_t m = (size_t)n + 1, L = 2 * (size_t)n, LZ = 2 * (size_t)nz, row = fold_y ? m : L;
   R* G = reinterpret_cast<R*>(out);
   for (size_t kx = 0; kx < m; ++kx)
-    for (size_t kz = 0; kz < L; ++kz) {
-      const size_t kzf = kz <= (size_t)n ? kz : L - kz;
+    for (size_t kz = 0; kz < LZ; ++kz) {
+      const size_t kzf = kz <= (size_t)nz ? kz : LZ - kz;
       const double c = scale / ((gx ? gx[kx] : 1.0) * (gz ? gz[kz] : 1.0));
       for (size_t ky = 0; ky < row; ++ky) {
         const size_t kyf = ky <= (size_t)n ? ky : L - ky;
-        const double cy = (fold_y || !gz) ? 1.0 : 1.0 / gz[ky];
-        G[(kx * L + kz) * row + ky] = (R)(c * cy * octant[(kx * m + kzf) * m + kyf]);
+        const double cy = (fold_y || !gy) ? 1.0 : 1.0 / gy[ky];
+        G[(kx * LZ + kz) * row + ky] = (R)(c * cy * octant[(kzf * m + kyf) * m + kx]);
       }
     }
   if (fold_y) {
     double* cy = reinterpret_cast<double*>(out + ktab_cy_offset(n, sizeof(R)));
-    for (size_t k = 0; k < L; ++k) cy[k] = gz ? 1.0 / gz[k] : 1.0;
+    for (size_t k = 0; k < L; ++k) cy[k] = gy ? 1.0 / gy[k] : 1.0;
   }
 }
 
-template <typename R, int N, bool PER = false> struct OpsImpl {
+// (N, PER): the x and y transforms; (NZ, PERZ): the z transform (mixed
+// boundary conditions: slab = periodic x, y with free z; wire = the reverse).
+template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> struct OpsImpl {
   using C = cplx<R>;
   static constexpr int G = PER ? 2 * N : N;  // grid points per axis
+  static constexpr bool mixed = NZ != N || PERZ != PER;
+  static_assert(G == (PERZ ? 2 * NZ : NZ), "one grid size on all axes");
   static constexpr int L = 2 * N;
   static constexpr int L1 = split_l1(L);
   static constexpr int L2 = L1 ? L / L1 : 1;
+  static constexpr int LZ = 2 * NZ;
+  static constexpr int LZ1 = split_l1(LZ);
+  static constexpr int LZ2 = LZ1 ? LZ / LZ1 : 1;
   static constexpr int X1 = split_x(N);
   static constexpr size_t slab = X1 ? (size_t)slab_elems(N, G) * sizeof(C) : 0;
   // two-CTA split: half the columns per CTA (the y-pass index split must fall
@@ -214,25 +224,39 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
   static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb, CL_A = SA.cl;
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb, CL_C = SC.cl;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
-  static constexpr int NW = zconv_warps(L2);
+  static constexpr int NW = zconv_warps(LZ2);
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
   // zconv: twiddles + column buffer, plus the staged kernel-table slice when
   // its rows are 16-byte aligned and three CTAs (the FP32 launch bound) still
   // fit in an SM's 228 KB of shared memory
-  static constexpr size_t smem_b0 = ((size_t)L + (size_t)L * W) * sizeof(C);
-  static constexpr size_t smem_g = (size_t)L * W * sizeof(R);
-  static constexpr size_t smem_bg = zconv_gsm_offset(L, W, sizeof(C)) + smem_g + 128;  // + alignment slack
+  static constexpr size_t smem_b0 = ((size_t)LZ + (size_t)LZ * W) * sizeof(C);
+  static constexpr size_t smem_g = (size_t)LZ * W * sizeof(R);
+  static constexpr size_t smem_bg = zconv_gsm_offset(LZ, W, sizeof(C)) + smem_g + 128;  // + alignment slack
   static constexpr bool stage_g = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 &&
-                                  (L * sizeof(R)) % 16 == 0 && L <= 256 &&
+                                  (L * sizeof(R)) % 16 == 0 && LZ <= 256 &&
                                   3 * (smem_bg + 1024) <= 228 * 1024;
   static constexpr size_t smem_b = stage_g ? smem_bg : smem_b0;
   // CTAs per SM the zconv register budget is sized for: three where shared
   // memory allows (FP32), else two
   static constexpr int MINB_B = (sizeof(R) == 4 && 3 * (smem_b + 1024) <= 228 * 1024) ? 3 : 2;
   // ky-folded kernel table where the unfolded one would exceed 24 MB
-  static constexpr bool fold_y = !stage_g && (size_t)(N + 1) * (2 * N) * (2 * N) * sizeof(R) > (24u << 20);
-  static constexpr bool ok = L1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
+  static constexpr bool fold_y = !mixed && !stage_g && (size_t)(N + 1) * (2 * N) * (2 * N) * sizeof(R) > (24u << 20);
+  static constexpr bool ok = L1 != 0 && LZ1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
+  template <bool EO> static constexpr auto zk() {
+    return &k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, EO, NZ, PERZ>;
+  }
+
+  // gains of the x and y transforms, and of the z transform
+  static void gains(double* gx, double* gy, double* gz) {
+    GainModel<N, PER>::gains(gx, gy);
+    if constexpr (!mixed) {
+      for (int k = 0; k < L; ++k) gz[k] = gy[k];
+    } else {
+      double tx[NZ + 1];
+      GainModel<NZ, PERZ>::gains(tx, gz);
+    }
+  }
 
   static cudaError_t setup() {
     if constexpr (ok) {
@@ -240,11 +264,9 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
       e = cudaFuncSetAttribute(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A, PER>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+      e = cudaFuncSetAttribute(zk<false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+      e = cudaFuncSetAttribute(zk<true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
       if (e != cudaSuccess) return e;
       return cudaFuncSetAttribute(k_inv_yx<R, N, NT_C, MINB_C, QC, CL_C, PER>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
@@ -266,13 +288,11 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
       CUtensorMap m{};
       if (stage_g && gmap) m = *gmap;
       if (energy_only)
-        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, true><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, m,
-            err);
+        zk<true>()<<<grid, 32 * NW, smem_b, st>>>(static_cast<C*>(X), static_cast<const R*>(Gs),
+                                                  static_cast<const C*>(tw), epart, m, err);
       else
-        k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, false><<<grid, 32 * NW, smem_b, st>>>(
-            static_cast<C*>(X), static_cast<const R*>(Gs), static_cast<const C*>(tw), epart, m,
-            err);
+        zk<false>()<<<grid, 32 * NW, smem_b, st>>>(static_cast<C*>(X), static_cast<const R*>(Gs),
+                                                   static_cast<const C*>(tw), epart, m, err);
     }
   }
   static void inv_yx(const void* X, void* V, const void* tw, int npair, cudaStream_t st) {
@@ -284,8 +304,10 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
   static Ops make() {
     Ops o;
     o.n = N;
+    o.nz = NZ;
     o.grid = G;
     o.periodic = PER;
+    o.periodic_z = PERZ;
     o.supported = ok;
     o.nyb = NYB;
     o.nt_a = NT_A;
@@ -297,7 +319,7 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
     o.setup = &setup;
     o.table_fold_y = fold_y;
     o.stage_table = stage_g;
-    if constexpr (ok && sizeof(R) == 4) o.gains = &GainModel<N, PER>::gains;
+    if constexpr (ok && sizeof(R) == 4) o.gains = &gains;
     o.fwd_xy = &fwd_xy;
     o.zconv = &zconv;
     o.inv_yx = &inv_yx;
@@ -316,6 +338,31 @@ template <typename R, int N, bool PER = false> struct OpsImpl {
   }                                                                 \
   const Ops* ops_pf64_##N() {                                       \
     static const Ops o = OpsImpl<double, N, true>::make();          \
+    return &o;                                                      \
+  }                                                                 \
+  }
+
+// slab (x, y periodic, z free) on a grid of 2N points per axis, and wire
+// (x, y free, z periodic) on a grid of N points per axis (N even)
+#define EXX_DEFINE_OPS_SLAB(N)                                      \
+  namespace exx {                                                   \
+  const Ops* ops_sf32_##N() {                                       \
+    static const Ops o = OpsImpl<float, N, true, 2 * N, false>::make(); \
+    return &o;                                                      \
+  }                                                                 \
+  const Ops* ops_sf64_##N() {                                       \
+    static const Ops o = OpsImpl<double, N, true, 2 * N, false>::make(); \
+    return &o;                                                      \
+  }                                                                 \
+  }
+#define EXX_DEFINE_OPS_WIRE(N)                                      \
+  namespace exx {                                                   \
+  const Ops* ops_wf32_##N() {                                       \
+    static const Ops o = OpsImpl<float, N, false, N / 2, true>::make(); \
+    return &o;                                                      \
+  }                                                                 \
+  const Ops* ops_wf64_##N() {                                       \
+    static const Ops o = OpsImpl<double, N, false, N / 2, true>::make(); \
     return &o;                                                      \
   }                                                                 \
   }

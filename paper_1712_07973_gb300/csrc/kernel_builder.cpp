@@ -67,7 +67,12 @@ void gauss_legendre(int m, std::vector<double>& x, std::vector<double>& w) {
 
 // Separable (t-node) spectrum: A[t][k] = gh(t,k) at the nodes of the t rule
 // on [t0, inf) (t0 = 0: full Coulomb kernel; t0 = omega h: erfc(omega r)/r).
-void sinc_factors(int n, double t0, std::vector<double>& A, std::vector<double>& wt) {
+// Optionally also AD[t][k], the windowed DFT of g(t,d) - g(t,0) (equal to A
+// for k != 0, without its cancellation where t is small), g(t,0) per node in
+// g0 and the nodes themselves in ts.
+void sinc_factors(int n, double t0, std::vector<double>& A, std::vector<double>& wt,
+                  std::vector<double>* AD = nullptr, std::vector<double>* g0 = nullptr,
+                  std::vector<double>* tsout = nullptr) {
   // composite Gauss-Legendre on q in [0, pi]: one panel per cosine period of
   // the largest distance, plus margin
   const int gl = 16;
@@ -108,11 +113,17 @@ void sinc_factors(int n, double t0, std::vector<double>& A, std::vector<double>&
   const int nt = (int)ts.size();
   A.assign((size_t)nt * (n + 1), 0.0);
   wt = ws;
-  std::vector<double> g(n + 1);
+  if (tsout) *tsout = ts;
+  if (AD) AD->assign((size_t)nt * (n + 1), 0.0);
+  if (g0) g0->assign(nt, 0.0);
+  std::vector<double> g(n + 1), D(n + 1);
   for (int it = 0; it < nt; ++it) {
     const double t = ts[it];
     if (t <= 0.2) {
-      for (int d = 0; d <= n; ++d) g[d] = std::exp(-t * t * (double)d * d);
+      for (int d = 0; d <= n; ++d) {
+        g[d] = std::exp(-t * t * (double)d * d);
+        D[d] = std::expm1(-t * t * (double)d * d);
+      }
     } else {
       std::vector<double> e(nq);
       for (int j = 0; j < nq; ++j) e[j] = qw[j] * std::exp(-q[j] * q[j] / (4.0 * t * t));
@@ -122,12 +133,18 @@ void sinc_factors(int n, double t0, std::vector<double>& A, std::vector<double>&
         for (int j = 0; j < nq; ++j) acc += e[j] * cq[(size_t)j * (n + 1) + d];
         g[d] = pre * acc;
       }
+      for (int d = 0; d <= n; ++d) D[d] = g[d] - g[0];
     }
     for (int k = 0; k <= n; ++k) {
-      double acc = 0.0;
-      for (int d = 0; d <= n; ++d) acc += ck[(size_t)k * (n + 1) + d] * g[d];
+      double acc = 0.0, accd = 0.0;
+      for (int d = 0; d <= n; ++d) {
+        acc += ck[(size_t)k * (n + 1) + d] * g[d];
+        accd += ck[(size_t)k * (n + 1) + d] * D[d];
+      }
       A[(size_t)it * (n + 1) + k] = acc;
+      if (AD) (*AD)[(size_t)it * (n + 1) + k] = accd;
     }
+    if (g0) (*g0)[it] = g[0];
   }
 }
 
@@ -217,15 +234,101 @@ void periodic_spectrum(int n, double h, double* out) {
       }
 }
 
+// Slab and wire boundary conditions (n even).  With
+// 4 pi / k^2 = int_0^inf (2 pi / t^3) e^{-k^2/(4t^2)} dt every axis contributes
+// one factor: on a free axis (zero-padded to 2n) the windowed DFT of the
+// band-limited 1D Gaussian, (t/sqrt(pi)) gh(t h, k) in the units above; on a
+// periodic axis e^{-k^2/(4t^2)} at k = 2 pi m / (n h).  In h = 1 units
+// (tau = t h, kappa = k h), per spectrum entry:
+//   slab:  Ghat = 2 sqrt(pi) h^2 int e^{-kappa^2/(4tau^2)} gh(tau, kz) / tau^2 dtau
+//   wire:  Ghat = 2 h^2 int e^{-kappa^2/(4tau^2)} gh(tau, kx) gh(tau, ky) / tau dtau
+// Each diverges at its (0, 0, 0) entry only (the 1D and 2D Coulomb potentials
+// have no finite mean); that entry is the windowed sum of the regularised
+// real-space kernel whose constant makes band-limited densities see exactly
+// -2 pi |z| (slab) or -2 ln(r / bohr) (wire):
+//   slab:  h^2 [2 sqrt(pi) int AD(tau, 0) / tau^2 dtau - 2n 4/pi]
+//   wire:  h^2 [2 int AD(tau, 0) (gh(tau, 0) + 2n g(tau, 0)) / tau dtau
+//               + (2n)^2 (2 ln(pi/h) + 2 gamma - 4 Catalan / pi)]
+// with AD the windowed DFT of g(tau, d) - g(tau, 0) (so that the t-integrals
+// converge at tau -> 0 without cancellation); for kz != 0 (slab) and kx or
+// ky != 0 (wire) the factor is taken from AD too.
+// Slab: out[(kz (n/2+1) + ky) (n/2+1) + kx], kz <= n, kx, ky <= n/2.
+// Wire: out[(kz (n+1) + ky) (n+1) + kx], kz <= n/2, kx, ky <= n.
+void slab_spectrum(int n, double h, double* out) {
+  std::vector<double> A, AD, wt, g0, ts;
+  sinc_factors(n, 0.0, A, wt, &AD, &g0, &ts);
+  const int nt = (int)wt.size(), m = n + 1, m2 = n / 2 + 1;
+  const double pre = 2.0 * std::sqrt(kPi) * h * h;
+  const double c = 2.0 * kPi / n;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int ky = 0; ky < m2; ++ky) {
+    std::vector<double> e(nt);
+    for (int kx = 0; kx <= ky; ++kx) {
+      const double kap2 = c * c * ((double)kx * kx + (double)ky * ky);
+      for (int it = 0; it < nt; ++it)
+        e[it] = wt[it] * std::exp(-kap2 / (4.0 * ts[it] * ts[it])) / (ts[it] * ts[it]);
+      for (int kz = 0; kz < m; ++kz) {
+        const std::vector<double>& F = (kz != 0 || kap2 == 0.0) ? AD : A;
+        double acc = 0.0;
+        for (int it = 0; it < nt; ++it) acc += e[it] * F[(size_t)it * m + kz];
+        double v = pre * acc;
+        if (kz == 0 && kap2 == 0.0) v -= h * h * 2.0 * n * 4.0 / kPi;
+        out[((size_t)kz * m2 + ky) * m2 + kx] = v;
+        out[((size_t)kz * m2 + kx) * m2 + ky] = v;
+      }
+    }
+  }
+}
+
+void wire_spectrum(int n, double h, double* out) {
+  std::vector<double> A, AD, wt, g0, ts;
+  sinc_factors(n, 0.0, A, wt, &AD, &g0, &ts);
+  const int nt = (int)wt.size(), m = n + 1, m2 = n / 2 + 1;
+  const double pre = 2.0 * h * h;
+  const double c = 2.0 * kPi / n;
+  const double kEulerGamma = 0.57721566490153286061, kCatalan = 0.91596559417721901505;
+  const double creg = 2.0 * std::log(kPi / h) + 2.0 * kEulerGamma - 4.0 * kCatalan / kPi;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int kz = 0; kz < m2; ++kz) {
+    const double kap2 = c * c * (double)kz * kz;
+    std::vector<double> e(nt);
+    for (int it = 0; it < nt; ++it)
+      e[it] = wt[it] * std::exp(-kap2 / (4.0 * ts[it] * ts[it])) / ts[it];
+    for (int ky = 0; ky < m; ++ky) {
+      const std::vector<double>& Fy = ky != 0 ? AD : A;
+      for (int kx = 0; kx <= ky; ++kx) {
+        const std::vector<double>& Fx = kx != 0 ? AD : A;
+        double v;
+        if (kap2 == 0.0 && kx == 0 && ky == 0) {
+          double acc = 0.0;
+          for (int it = 0; it < nt; ++it)
+            acc += e[it] * AD[(size_t)it * m] * (A[(size_t)it * m] + 2.0 * n * g0[it]);
+          v = pre * acc + h * h * (2.0 * n) * (2.0 * n) * creg;
+        } else {
+          double acc = 0.0;
+          for (int it = 0; it < nt; ++it)
+            acc += e[it] * Fx[(size_t)it * m + kx] * Fy[(size_t)it * m + ky];
+          v = pre * acc;
+        }
+        out[((size_t)kz * m + ky) * m + kx] = v;
+        out[((size_t)kz * m + kx) * m + ky] = v;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 // kind: 0 = band-limited (sinc), 1 = Hockney, 2 = band-limited erfc(omega r)/r
-// (omega > 0): out (n+1)^3 doubles; 3 = periodic (n even): out (n/2+1)^3.
+// (omega > 0): out (n+1)^3 doubles; 3 = periodic (n even): out (n/2+1)^3;
+// 4 = slab (n even): out (n+1) (n/2+1)^2; 5 = wire (n even): out (n/2+1) (n+1)^2.
 bool kernel_spectrum_octant(int n, double h, int kind, double omega, double* out) {
   if (n < 1 || !(h > 0.0) || out == nullptr) return false;
-  if (kind == 3) {
+  if (kind == 3 || kind == 4 || kind == 5) {
     if (n % 2 != 0) return false;
-    periodic_spectrum(n, h, out);
+    if (kind == 3) periodic_spectrum(n, h, out);
+    else if (kind == 4) slab_spectrum(n, h, out);
+    else wire_spectrum(n, h, out);
     return true;
   }
   if (kind == 0) sinc_spectrum(n, h, 0.0, out);

@@ -15,10 +15,10 @@ from . import build as _build
 
 __all__ = ["ExxError", "ExxPlan", "ExxBatch", "load_library", "kernel_spectrum", "shard_tiles", "EXPORTS",
            "FP64", "FP32", "KERNEL_SINC", "KERNEL_HOCKNEY", "KERNEL_ERFC", "KERNEL_PERIODIC",
-           "FLAG_VX_FP64"]
+           "KERNEL_SLAB", "KERNEL_WIRE", "FLAG_VX_FP64"]
 
 FP64, FP32 = 0, 1
-KERNEL_SINC, KERNEL_HOCKNEY, KERNEL_ERFC, KERNEL_PERIODIC = 0, 1, 2, 3
+KERNEL_SINC, KERNEL_HOCKNEY, KERNEL_ERFC, KERNEL_PERIODIC, KERNEL_SLAB, KERNEL_WIRE = range(6)
 FLAG_VX_FP64 = 1
 STATUS = ["EXX_OK", "EXX_ERR_INVALID_ARG", "EXX_ERR_CUDA", "EXX_ERR_OOM", "EXX_ERR_TIMEOUT",
           "EXX_ERR_NOT_SUPPORTED"]
@@ -112,13 +112,17 @@ def _check(status, where, plan=None):
 
 
 def kernel_spectrum(n, h, kind=KERNEL_SINC, omega=0.0):
-    """Host-only FP64 octant of the kernel spectrum: (n+1,)*3 for the padded
-    free-boundary kernels, (n/2+1,)*3 for KERNEL_PERIODIC."""
-    m = n // 2 + 1 if kind == KERNEL_PERIODIC else n + 1
-    out = np.zeros(m ** 3, dtype=np.float64)
+    """Host-only FP64 octant of the kernel spectrum, indexed [kz][ky][kx]:
+    (n+1,)*3 for the padded free-boundary kernels, (n/2+1,)*3 for
+    KERNEL_PERIODIC, (n+1, n/2+1, n/2+1) for KERNEL_SLAB and
+    (n/2+1, n+1, n+1) for KERNEL_WIRE (a periodic axis runs to n/2)."""
+    half, full = n // 2 + 1, n + 1
+    shape = {KERNEL_PERIODIC: (half,) * 3, KERNEL_SLAB: (full, half, half),
+             KERNEL_WIRE: (half, full, full)}.get(int(kind), (full,) * 3)
+    out = np.zeros(int(np.prod(shape)), dtype=np.float64)
     _check(load_library().exx_kernel_spectrum(n, float(h), int(kind), float(omega),
                                               out.ctypes.data_as(_c_double_p)), "exx_kernel_spectrum")
-    return out.reshape(m, m, m)
+    return out.reshape(shape)
 
 
 def shard_tiles(norb, tile=0, nranks=1):
@@ -160,8 +164,10 @@ class ExxPlan:
     """Plan of the exact-exchange operator for fixed grid, h, alpha and occupations.
 
     precision: "fp64" (psi/vxpsi double) or "fp32" (psi float; vxpsi float, or
-    double with vx_fp64=True).  kernel: "sinc" (band-limited), "hockney", or
-    "erfc" (band-limited erfc(omega r)/r, screened hybrids; needs omega > 0).
+    double with vx_fp64=True).  kernel: "sinc" (band-limited), "hockney",
+    "erfc" (band-limited erfc(omega r)/r, screened hybrids; needs omega > 0),
+    "periodic" (the n^3 cell repeats), "slab" (x, y periodic, z free) or
+    "wire" (x, y free, z periodic).
     tile: pair-tile edge 1..8 (0: the library default; "auto": the tuned value).
     """
 
@@ -179,7 +185,7 @@ class ExxPlan:
         self.norb = int(occ.size)
         self.precision = {"fp64": FP64, "fp32": FP32}[precision]
         self.kernel = {"sinc": KERNEL_SINC, "hockney": KERNEL_HOCKNEY, "erfc": KERNEL_ERFC,
-                       "periodic": KERNEL_PERIODIC}[kernel]
+                       "periodic": KERNEL_PERIODIC, "slab": KERNEL_SLAB, "wire": KERNEL_WIRE}[kernel]
         self.omega = float(omega)
         self.vx_fp64 = bool(vx_fp64)
         self.dtype = torch.float64 if self.precision == FP64 else torch.float32

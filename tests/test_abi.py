@@ -98,7 +98,7 @@ def test_kernel_spectrum_rejects_bad_arguments(lib):
     p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     assert lib.exx_kernel_spectrum(0, 0.4, 0, 0.0, p) == 1
     assert lib.exx_kernel_spectrum(1, -1.0, 0, 0.0, p) == 1
-    assert lib.exx_kernel_spectrum(1, 0.4, 4, 0.0, p) == 1
+    assert lib.exx_kernel_spectrum(1, 0.4, 6, 0.0, p) == 1
     assert lib.exx_kernel_spectrum(1, 0.4, 0, 0.0, None) == 1
     assert lib.exx_kernel_spectrum(1, 0.4, 2, 0.0, p) == 1   # erfc needs omega > 0
     assert lib.exx_kernel_spectrum(1, 0.4, 2, -0.1, p) == 1
@@ -134,3 +134,30 @@ def test_periodic_needs_even_supported_grid(lib):
     assert _create(lib, grid=(10, 10, 10), kernel=3)[0] == 5   # 10 not compiled
     out = np.zeros(8)
     assert lib.exx_kernel_spectrum(3, 0.4, 3, 0.0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
+
+
+@pytest.mark.parametrize("n,h", [(8, 0.4), (16, 0.3), (48, 0.2)])
+def test_host_slab_and_wire_spectra_match_oracle(lib, n, h):
+    # library: t-separable spectral factors with exp-sinh nodes and the
+    # regularised (0,0,0) entries; oracle: Faddeeva factors, trapezoid in ln t,
+    # and the sine-integral closed form of the slab's k = 0 kernel
+    from paper_1712_07973_gb300 import exx
+    m, m2 = n + 1, n // 2 + 1
+    got = exx.kernel_spectrum(n, h, exx.KERNEL_SLAB)         # [kz][ky][kx], kz <= n
+    ref = o.kernel_spectrum_slab(n, h)[:m, :m2, :m2]
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    got = exx.kernel_spectrum(n, h, exx.KERNEL_WIRE)         # [kz][ky][kx], kz <= n/2
+    ref = o.kernel_spectrum_wire(n, h)[:m2, :m, :m]
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_slab_and_wire_need_even_supported_grid(lib):
+    for kernel in (4, 5):
+        assert _create(lib, grid=(9, 9, 9), kernel=kernel)[0] == 5
+        assert _create(lib, grid=(12, 12, 12), kernel=kernel)[0] == 5   # not compiled
+        out = np.zeros(8)
+        assert lib.exx_kernel_spectrum(3, 0.4, kernel, 0.0,
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
+    assert _create(lib, kernel=6)[0] == 1

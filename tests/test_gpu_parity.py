@@ -54,6 +54,10 @@ def _oracle(psi, occ, alpha, h, kernel=o.KERNEL_SINC, omega=0.0):
     n = psi.shape[1]
     if kernel == "periodic":
         Gh = o.kernel_spectrum_periodic(n, h)
+    elif kernel == "slab":
+        Gh = o.kernel_spectrum_slab(n, h)
+    elif kernel == "wire":
+        Gh = o.kernel_spectrum_wire(n, h)
     else:
         Gh = o.kernel_spectrum(o.kernel_real_space(n, h, kernel, omega=omega))
     Ex, vx, Eij = o.exx(psi, occ, alpha, h, Gh)
@@ -357,6 +361,43 @@ def test_periodic_fp32_192(torch_dev):
     assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6, (E, Ee, Eo)
     assert np.max(np.abs(Eij - Eijo)) <= 1e-6
     assert np.max(np.abs(vx - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+
+
+# ------------------------------------------ slab and wire boundary conditions
+# slab: x, y periodic (the periodic transforms), z free (the padded, pruned
+# z transform); wire: x, y free, z periodic.  The zconv kernel then runs a z
+# line of another length than the x and y lines.
+
+@pytest.mark.parametrize("kernel", ["slab", "wire"])
+@pytest.mark.parametrize("n", [8, 16, 32, 48])
+def test_slab_wire_fp64(torch_dev, kernel, n):
+    psi = _orbitals(n, 3, seed=130 + n, h=0.45)
+    occ = np.array([2.0, 1.5, 2.0])
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.45, "fp64", kernel=kernel),
+                 _oracle(psi, occ, 0.25, 0.45, kernel))
+
+
+@pytest.mark.parametrize("kernel", ["slab", "wire"])
+def test_slab_wire_fp64_several_tiles(torch_dev, kernel):
+    # 10 orbitals: three tiles of 8 + 2 (ragged), off-diagonal and diagonal
+    psi = _orbitals(16, 10, seed=151, h=0.4)
+    occ = np.linspace(0.5, 2.0, 10)
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.4, "fp64", kernel=kernel),
+                 _oracle(psi, occ, 0.25, 0.4, kernel))
+
+
+@pytest.mark.parametrize("kernel", ["slab", "wire"])
+@pytest.mark.parametrize("n,prec", [(64, "fp32"), (96, "fp32"), (96, "fp64")])
+def test_slab_wire_larger_grids(torch_dev, kernel, n, prec):
+    psi = _orbitals(n, 3, seed=160 + n, h=0.4)
+    occ = np.full(3, 2.0)
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, 0.25, 0.4, prec, kernel=kernel)
+    Eo, vxo, Eijo = _oracle(psi, occ, 0.25, 0.4, kernel)
+    tol = 1e-10 * abs(Eo) if prec == "fp64" else 1e-6
+    assert abs(E - Eo) <= tol and abs(Ee - Eo) <= tol, (E, Ee, Eo)
+    assert np.max(np.abs(Eij - Eijo)) <= (1e-10 * np.max(np.abs(Eijo)) if prec == "fp64" else 1e-6)
+    vt = 1e-10 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(vx - vxo)) <= vt * np.max(np.abs(vxo))
 
 
 def test_bounded_wait_times_out_and_context_survives(torch_dev, monkeypatch):
