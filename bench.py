@@ -382,6 +382,14 @@ def run_ours(a):
                 "traffic": committed_traffic(dom), "algorithmic_bytes_per_launch": int(per_launch_bytes),
                 "avg_launch_ms": kms / kcnt, "kernel_shares": shares}
 
+    # whole pipeline: algorithmic bytes of all kernels of a step over the step time
+    step_bytes = sum(alg.values())
+    pipeline = {"algorithmic_bytes_per_step": int(step_bytes),
+                "bytes_per_pair": int(step_bytes / P),
+                "achieved": round(step_bytes / (ms_step * 1e-3) / 1e9, 1), "unit": "GB/s",
+                "frac": round(step_bytes / (ms_step * 1e-3) / 1e9 / peak, 4)}
+    roofline["pipeline"] = pipeline
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

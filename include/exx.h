@@ -189,8 +189,13 @@ exx_status_t exx_plan_info(exx_plan_t plan, int* tile, int* ntiles, size_t* work
  *   vxpsi_host  host, same shape, dtype as for exx_apply; overwritten.
  *   E_out       host, may be NULL.
  * The first call allocates device buffers for psi and vxpsi inside the plan
- * (kept until exx_plan_destroy).  The call copies psi in, runs exx_apply on
- * the stream, copies vxpsi and E_x out, and synchronises the stream.
+ * (kept until exx_plan_destroy), a copy stream and events.  The call copies
+ * psi in per block of T orbitals (the tile edge) on the copy stream, runs
+ * exx_apply on the given stream with each tile waiting only for its two
+ * blocks, copies each block of vxpsi out as soon as the last tile row that
+ * touches it has finished (row-major tiles: block b after row b), copies E_x
+ * out and synchronises both streams before returning.  Results equal those
+ * of exx_apply bit for bit.  A sharded plan copies in one piece each way.
  */
 exx_status_t exx_apply_host(exx_plan_t plan, const void* psi_host, void* vxpsi_host, double* E_out,
                             void* cuda_stream);

@@ -249,6 +249,10 @@ struct exx_plan_s {
   CUtensorMap gmap{};      // TMA descriptor of the kernel table (Ops::stage_table)
   void* h_psi = nullptr;  // exx_apply_host staging (allocated on first use)
   void* h_vx = nullptr;
+  // exx_apply_host overlap: copy stream, per-orbital-block events
+  cudaStream_t cst = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_join = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_out;
   // per-kernel event timing (exx_profile_enable)
   bool prof = false;
   std::vector<cudaEvent_t> ev[EXX_NKINDS];  // start/stop pairs, in launch order
@@ -280,6 +284,11 @@ void free_plan(exx_plan_t p) {
     if (q) cudaFree(q);
   for (int k = 0; k < EXX_NKINDS; ++k)
     for (cudaEvent_t e : p->ev[k]) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_in) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_out) cudaEventDestroy(e);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->cst) cudaStreamDestroy(p->cst);
 }
 
 enum Kind { K_FWD = 0, K_ZCONV = 1, K_PAIRE = 2, K_INV = 3, K_ACCUM = 4, K_TOTAL = 5, K_CONV = 6 };
@@ -579,8 +588,18 @@ exx_status_t exx_plan_info(exx_plan_t p, int* tile, int* ntiles, size_t* workspa
 }
 
 
+// Host-buffer overlap (exx_apply_host): tiles wait for the input events of
+// their two orbital blocks (recorded by the copy stream after each block's
+// host-to-device copy), and when a tile row ends, the vx of its block is
+// complete (row-major tiles bi <= bj: block b appears only in rows <= b), so
+// it is converted and handed to the copy stream through ev_out[b].
+struct HostOverlap {
+  const std::vector<cudaEvent_t>* in;
+  const std::vector<cudaEvent_t>* out;
+};
+
 static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_dev, bool apply,
-                        cudaStream_t st) {
+                        cudaStream_t st, const HostOverlap* ov = nullptr) {
   const int n = p->n, N = p->N;
   const long long n3 = (long long)n * n * n;
   const double h3 = p->h * p->h * p->h;
@@ -594,10 +613,15 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
   const double c = -p->alpha;
   if (p->sharded)  // pair energies of other ranks' tiles must read as zero
     EXX_CUDA(p, cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st));
+  int waited = -1;  // input blocks 0..waited are known to have arrived
   for (size_t ti = 0; ti < p->tiles.size(); ++ti) {
     if (!p->mine[ti]) continue;
     const Tile& t = p->tiles[ti];
     const int4* pr = p->d_pairs + t.off;
+    if (ov) {
+      const int bj = t.j0 / p->T;
+      while (waited < bj) EXX_CUDA(p, cudaStreamWaitEvent(st, (*ov->in)[++waited], 0));
+    }
     {
       ProfScope ps(p, K_FWD, st);
       p->ops->fwd_xy(psi, nullptr, pr, t.count, p->X2, p->tw, n3, st);
@@ -630,12 +654,24 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
         launch_accum<float>(v2, mode, static_cast<const float*>(psi),
                             static_cast<const float*>(p->V), acc, p->d_occ, t, c, n3, st);
     }
+    const bool row_end = ti + 1 == p->tiles.size() || p->tiles[ti + 1].i0 != t.i0;
+    if (ov && apply && row_end) {
+      const int b = t.i0 / p->T;
+      if (p->vacc) {
+        ProfScope ps(p, K_CONV, st);
+        const long long cnt = (long long)t.ti * n3, off = (long long)t.i0 * n3;
+        long long blocks = (cnt + 255) / 256;
+        if (blocks > 152 * 32) blocks = 152 * 32;
+        k_to_float<<<(int)blocks, 256, 0, st>>>(p->vacc + off, static_cast<float*>(vxpsi) + off, cnt);
+      }
+      EXX_CUDA(p, cudaEventRecord((*ov->out)[b], st));
+    }
   }
   {
     ProfScope ps(p, K_TOTAL, st);
     k_exx_total<<<1, 256, 0, st>>>(p->Epair, p->P, N, p->d_occ, p->alpha, E_dev ? E_dev : p->E_dev);
   }
-  if (apply && p->vacc) {
+  if (apply && p->vacc && !ov) {
     ProfScope ps(p, K_CONV, st);
     const long long tot = (long long)N * n3;
     long long blocks = (tot + 255) / 256;
@@ -703,11 +739,56 @@ exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host
     exx_status_t s = dalloc(p, &p->h_vx, cnt * vs);
     if (s != EXX_OK) return s;
   }
-  EXX_CUDA(p, cudaMemcpyAsync(p->h_psi, psi_host, cnt * ps, cudaMemcpyHostToDevice, st));
-  exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st);
-  if (s != EXX_OK) return s;
-  EXX_CUDA(p, cudaMemcpyAsync(vxpsi_host, p->h_vx, cnt * vs, cudaMemcpyDeviceToHost, st));
+  if (p->sharded) {  // partial results: one copy each way around the pipeline
+    EXX_CUDA(p, cudaMemcpyAsync(p->h_psi, psi_host, cnt * ps, cudaMemcpyHostToDevice, st));
+    exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st);
+    if (s != EXX_OK) return s;
+    EXX_CUDA(p, cudaMemcpyAsync(vxpsi_host, p->h_vx, cnt * vs, cudaMemcpyDeviceToHost, st));
+    if (E_out) EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return check_wait_flag(p, st);
+  }
+  // copies per orbital block on a second stream, overlapped with the tiles:
+  // block b goes in ahead of the first tile that reads it, and its vx goes
+  // out as soon as the last tile row that touches it has finished
+  const int nb = (p->N + p->T - 1) / p->T;
+  if (p->cst == nullptr)
+    EXX_CUDA(p, cudaStreamCreateWithFlags(&p->cst, cudaStreamNonBlocking));
+  auto mk = [&](cudaEvent_t* e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
+  if (p->ev_start == nullptr) EXX_CUDA(p, mk(&p->ev_start));
+  if (p->ev_join == nullptr) EXX_CUDA(p, mk(&p->ev_join));
+  while ((int)p->ev_in.size() < nb) {
+    cudaEvent_t a, b;
+    EXX_CUDA(p, mk(&a));
+    p->ev_in.push_back(a);
+    EXX_CUDA(p, mk(&b));
+    p->ev_out.push_back(b);
+  }
+  const size_t blk = (size_t)p->T * p->n * p->n * p->n;  // elements per orbital block
+  EXX_CUDA(p, cudaEventRecord(p->ev_start, st));  // earlier work on st is done first
+  EXX_CUDA(p, cudaStreamWaitEvent(p->cst, p->ev_start, 0));
+  for (int b = 0; b < nb; ++b) {
+    const size_t off = (size_t)b * blk, len = std::min(blk, cnt - off);
+    EXX_CUDA(p, cudaMemcpyAsync(static_cast<char*>(p->h_psi) + off * ps,
+                                static_cast<const char*>(psi_host) + off * ps, len * ps,
+                                cudaMemcpyHostToDevice, p->cst));
+    EXX_CUDA(p, cudaEventRecord(p->ev_in[b], p->cst));
+  }
+  HostOverlap ov{&p->ev_in, &p->ev_out};
+  exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st, &ov);
+  if (s != EXX_OK) {
+    cudaStreamSynchronize(p->cst);
+    return s;
+  }
+  for (int b = 0; b < nb; ++b) {
+    const size_t off = (size_t)b * blk, len = std::min(blk, cnt - off);
+    EXX_CUDA(p, cudaStreamWaitEvent(p->cst, p->ev_out[b], 0));
+    EXX_CUDA(p, cudaMemcpyAsync(static_cast<char*>(vxpsi_host) + off * vs,
+                                static_cast<const char*>(p->h_vx) + off * vs, len * vs,
+                                cudaMemcpyDeviceToHost, p->cst));
+  }
   if (E_out) EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  EXX_CUDA(p, cudaEventRecord(p->ev_join, p->cst));
+  EXX_CUDA(p, cudaStreamWaitEvent(st, p->ev_join, 0));
   return check_wait_flag(p, st);
 }
 

@@ -428,3 +428,67 @@ def test_fp64_two_cta_slabs_320_threads(torch_dev, n):
     psi = _orbitals(n, 2, seed=40 + n, h=0.35)
     occ = np.array([2.0, 1.0])
     _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.35, "fp64"), _oracle(psi, occ, 0.25, 0.35))
+
+
+def test_apply_captured_in_a_cuda_graph(torch_dev):
+    # the asynchronous entry point enqueues only kernels and device copies on
+    # the caller's stream, so a whole exx_apply can be captured once and
+    # replayed; replays equal eager calls bit for bit and follow new inputs
+    # written into the captured buffer
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    psi = _orbitals(24, 10, seed=171, h=0.45)
+    occ = np.full(10, 2.0)
+    plan = exx.ExxPlan(24, 0.45, 0.25, occ, precision="fp32")
+    p = torch.from_numpy(psi).to(dev, torch.float32)
+    out = torch.empty_like(p)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    plan.apply_async(p, out, E)
+    torch.cuda.synchronize()
+    out_ref, E_ref = out.clone(), E.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.apply_async(p, out, E)  # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.apply_async(p, out, E)
+    out.zero_()
+    E.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, out_ref) and torch.equal(E, E_ref)
+    p.mul_(2.0)  # E x16, Vx psi x8
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(E) == pytest.approx(16.0 * float(E_ref), rel=1e-6)
+    assert torch.allclose(out, 8.0 * out_ref, rtol=1e-5, atol=1e-6 * float(out_ref.abs().max()))
+    plan.close()
+
+
+@pytest.mark.parametrize("prec,vx_fp64,N", [("fp32", False, 10), ("fp32", True, 19), ("fp64", False, 10),
+                                             ("fp32", False, 5)])
+def test_host_buffer_entry_point_overlapped_copies(torch_dev, prec, vx_fp64, N):
+    # exx_apply_host copies the orbitals in per block of T orbitals on a second
+    # stream, overlapped with the tiles, and sends each block's Vx psi back as
+    # soon as its last tile row is done: results equal the device entry point
+    # bit for bit (same kernels, same order); ragged last blocks included
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    n = 16
+    psi = _orbitals(n, N, seed=180 + N, h=0.45)
+    occ = np.linspace(1.0, 2.0, N)
+    plan = exx.ExxPlan(n, 0.45, 0.25, occ, precision=prec, vx_fp64=vx_fp64)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    p = torch.from_numpy(psi).to(dev, dt)
+    E, vx = plan.apply(p)
+    ph = p.cpu().pin_memory()
+    vh = torch.empty(vx.shape, dtype=vx.dtype).pin_memory()
+    for _ in range(2):  # the second call reuses the staging buffers and events
+        vh.fill_(float("nan"))
+        Eh = plan.apply_host(ph, vh)
+        assert Eh == E
+        assert torch.equal(vh, vx.cpu())
+    plan.close()
