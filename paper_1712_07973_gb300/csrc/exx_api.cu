@@ -249,6 +249,13 @@ struct exx_plan_s {
   CUtensorMap gmap{};      // TMA descriptor of the kernel table (Ops::stage_table)
   void* h_psi = nullptr;  // exx_apply_host staging (allocated on first use)
   void* h_vx = nullptr;
+  // two pipeline lanes: lane 1's workspaces, streams and events
+  int lanes = 1;
+  void* X2b = nullptr;
+  void* Vb = nullptr;
+  double* epartb = nullptr;
+  cudaStream_t ls[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_done[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // exx_apply_host overlap: copy stream, per-orbital-block events
   cudaStream_t cst = nullptr;
   cudaEvent_t ev_start = nullptr, ev_join = nullptr;
@@ -289,6 +296,14 @@ void free_plan(exx_plan_t p) {
   if (p->ev_start) cudaEventDestroy(p->ev_start);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->cst) cudaStreamDestroy(p->cst);
+  for (void* q : {p->X2b, p->Vb, static_cast<void*>(p->epartb)})
+    if (q) cudaFree(q);
+  for (int l = 0; l < 2; ++l) {
+    if (p->ls[l]) cudaStreamDestroy(p->ls[l]);
+    if (p->ev_done[l]) cudaEventDestroy(p->ev_done[l]);
+    if (p->ev_free[l]) cudaEventDestroy(p->ev_free[l]);
+  }
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
 }
 
 enum Kind { K_FWD = 0, K_ZCONV = 1, K_PAIRE = 2, K_INV = 3, K_ACCUM = 4, K_TOTAL = 5, K_CONV = 6 };
@@ -530,6 +545,17 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   }
   EXX_ALLOC(p->E_dev, sizeof(double));
   EXX_ALLOC(p->d_err, 2 * sizeof(int));
+  // second pipeline lane (EXX_LANES=1 turns it off) where the plan has more
+  // than one tile
+  {
+    const char* env = std::getenv("EXX_LANES");
+    p->lanes = (env && env[0] == '1') ? 1 : (p->tiles.size() > 1 ? 2 : 1);
+  }
+  if (p->lanes > 1) {
+    EXX_ALLOC(p->epartb, (size_t)p->maxpairs * nper * sizeof(double));
+    EXX_ALLOC(p->X2b, (size_t)p->maxpairs * m * n * (2 * nh) * cs);
+    EXX_ALLOC(p->Vb, (size_t)p->maxpairs * n3 * rs);
+  }
 #undef EXX_ALLOC
 
   cudaError_t e = cudaMemcpyAsync(p->Gs, gbuf.data(), gbuf.size(), cudaMemcpyHostToDevice, st);
@@ -556,6 +582,14 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&p->gmap, p->Gs, nh, nz))
     e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = ops->setup();
+  if (e == cudaSuccess && p->lanes > 1) {
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+      e = cudaStreamCreateWithFlags(&p->ls[l], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done[l], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_free[l], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_plan(p);
@@ -613,34 +647,61 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
   const double c = -p->alpha;
   if (p->sharded)  // pair energies of other ranks' tiles must read as zero
     EXX_CUDA(p, cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st));
-  int waited = -1;  // input blocks 0..waited are known to have arrived
+  // Two lanes: consecutive tiles alternate between two streams with their own
+  // spectrum, potential and partial-energy buffers, so that the transforms of
+  // one tile run beside those of the next; the accumulation stays on the
+  // caller's stream in tile order (identical sums, no two updates of one
+  // accumulator at a time), and a lane overwrites its V only after the
+  // accumulation of its previous tile has read it.
+  const int nl = p->lanes;
+  if (nl > 1) {
+    EXX_CUDA(p, cudaEventRecord(p->ev_fork, st));
+    for (int l = 0; l < nl; ++l) EXX_CUDA(p, cudaStreamWaitEvent(p->ls[l], p->ev_fork, 0));
+  }
+  void* X2l[2] = {p->X2, p->X2b};
+  void* Vl[2] = {p->V, p->Vb};
+  double* epl[2] = {p->epart, p->epartb};
+  bool used[2] = {false, false};
+  int waited[2] = {-1, -1};  // per lane: input blocks 0..waited are known to have arrived
+  int k = 0;
   for (size_t ti = 0; ti < p->tiles.size(); ++ti) {
     if (!p->mine[ti]) continue;
     const Tile& t = p->tiles[ti];
     const int4* pr = p->d_pairs + t.off;
+    const int l = nl > 1 ? (k++ & 1) : 0;
+    cudaStream_t sl = nl > 1 ? p->ls[l] : st;
+    void* X2 = X2l[l];
+    void* Vt = Vl[l];
+    double* ep = epl[l];
     if (ov) {
       const int bj = t.j0 / p->T;
-      while (waited < bj) EXX_CUDA(p, cudaStreamWaitEvent(st, (*ov->in)[++waited], 0));
+      while (waited[l] < bj) EXX_CUDA(p, cudaStreamWaitEvent(sl, (*ov->in)[++waited[l]], 0));
     }
     {
-      ProfScope ps(p, K_FWD, st);
-      p->ops->fwd_xy(psi, nullptr, pr, t.count, p->X2, p->tw, n3, st);
+      ProfScope ps(p, K_FWD, sl);
+      p->ops->fwd_xy(psi, nullptr, pr, t.count, X2, p->tw, n3, sl);
     }
     {
-      ProfScope ps(p, K_ZCONV, st);
-      p->ops->zconv(p->X2, p->Gs, p->twz ? p->twz : p->tw, &p->gmap, p->epart, p->d_err, t.count,
-                    !apply, st);
+      ProfScope ps(p, K_ZCONV, sl);
+      p->ops->zconv(X2, p->Gs, p->twz ? p->twz : p->tw, &p->gmap, ep, p->d_err, t.count, !apply,
+                    sl);
     }
     {
-      ProfScope ps(p, K_PAIRE, st);
-      k_pair_energy<<<(t.count * 32 + 255) / 256, 256, 0, st>>>(p->epart, nper, pr, t.count, h3,
+      ProfScope ps(p, K_PAIRE, sl);
+      k_pair_energy<<<(t.count * 32 + 255) / 256, 256, 0, sl>>>(ep, nper, pr, t.count, h3,
                                                                   p->Epair);
     }
     if (apply) {
+      if (nl > 1 && used[l]) EXX_CUDA(p, cudaStreamWaitEvent(sl, p->ev_free[l], 0));
       {
-        ProfScope ps(p, K_INV, st);
-        p->ops->inv_yx(p->X2, p->V, p->tw, t.count, st);
+        ProfScope ps(p, K_INV, sl);
+        p->ops->inv_yx(X2, Vt, p->tw, t.count, sl);
       }
+      if (nl > 1) {
+        EXX_CUDA(p, cudaEventRecord(p->ev_done[l], sl));
+        EXX_CUDA(p, cudaStreamWaitEvent(st, p->ev_done[l], 0));
+      }
+      used[l] = true;
       ProfScope ps(p, K_ACCUM, st);
       // vector width: 2 values per thread when n^3 and the caller's pointers
       // allow aligned vector accesses
@@ -649,10 +710,11 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
       const int mode = (t.ti == 8 && t.tj == 8) ? (t.diag ? 2 : 1) : 0;
       if (p->prec == EXX_FP64)
         launch_accum<double>(v2, mode, static_cast<const double*>(psi),
-                             static_cast<const double*>(p->V), acc, p->d_occ, t, c, n3, st);
+                             static_cast<const double*>(Vt), acc, p->d_occ, t, c, n3, st);
       else
         launch_accum<float>(v2, mode, static_cast<const float*>(psi),
-                            static_cast<const float*>(p->V), acc, p->d_occ, t, c, n3, st);
+                            static_cast<const float*>(Vt), acc, p->d_occ, t, c, n3, st);
+      if (nl > 1) EXX_CUDA(p, cudaEventRecord(p->ev_free[l], st));
     }
     const bool row_end = ti + 1 == p->tiles.size() || p->tiles[ti + 1].i0 != t.i0;
     if (ov && apply && row_end) {
@@ -667,6 +729,11 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
       EXX_CUDA(p, cudaEventRecord((*ov->out)[b], st));
     }
   }
+  if (nl > 1)  // join: every lane's pair energies (and, for apply, V reads) are done
+    for (int l = 0; l < nl; ++l) {
+      EXX_CUDA(p, cudaEventRecord(p->ev_done[l], p->ls[l]));
+      EXX_CUDA(p, cudaStreamWaitEvent(st, p->ev_done[l], 0));
+    }
   {
     ProfScope ps(p, K_TOTAL, st);
     k_exx_total<<<1, 256, 0, st>>>(p->Epair, p->P, N, p->d_occ, p->alpha, E_dev ? E_dev : p->E_dev);

@@ -492,3 +492,27 @@ def test_host_buffer_entry_point_overlapped_copies(torch_dev, prec, vx_fp64, N):
         assert Eh == E
         assert torch.equal(vh, vx.cpu())
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_two_lane_pipeline_equals_one_lane(torch_dev, monkeypatch, prec):
+    # consecutive tiles alternate between two streams with their own
+    # workspaces while the accumulation stays in tile order on the caller's
+    # stream: energies, pair energies and Vx psi are identical bit for bit
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    psi = _orbitals(24, 20, seed=191, h=0.45)   # 3 blocks, 6 tiles, ragged last block
+    occ = np.linspace(0.5, 2.0, 20)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    p = torch.from_numpy(psi).to(dev, dt)
+    res = []
+    for lanes in ("1", "2"):
+        monkeypatch.setenv("EXX_LANES", lanes)
+        plan = exx.ExxPlan(24, 0.45, 0.25, occ, precision=prec)
+        E, vx = plan.apply(p)
+        res.append((E, plan.energy(p), vx.cpu(), plan.pair_energies()))
+        plan.close()
+    (E1, Ee1, v1, P1), (E2, Ee2, v2, P2) = res
+    assert E1 == E2 and Ee1 == Ee2
+    assert torch.equal(v1, v2)
+    assert np.array_equal(P1, P2)
