@@ -201,6 +201,22 @@ exx_status_t exx_apply_host(exx_plan_t plan, const void* psi_host, void* vxpsi_h
                             void* cuda_stream);
 
 /*
+ * exx_plan_set_lanes -- number of pipeline lanes (1 or 2) of later calls.
+ * With two lanes (the default where the plan has more than one pair tile and
+ * the environment variable EXX_LANES is not "1" at plan creation) consecutive
+ * tiles alternate between two internal streams with their own spectrum and
+ * potential workspaces, so the transforms of one tile run beside those of
+ * the next; the accumulation stays on the caller's stream in tile order and
+ * results are identical bit for bit.  One lane serialises every kernel on the
+ * caller's stream (per-kernel timing, below, then measures each kernel
+ * alone).  Returns EXX_ERR_NOT_SUPPORTED for 2 when the plan was created
+ * with one lane.
+ */
+exx_status_t exx_plan_set_lanes(exx_plan_t plan, int lanes);
+/* exx_plan_get_lanes -- current number of lanes (host out-parameter). */
+exx_status_t exx_plan_get_lanes(exx_plan_t plan, int* lanes);
+
+/*
  * Per-kernel timing with CUDA events recorded on the launching stream around
  * every launch of the pipeline (kernel kinds, in order: 0 fwd_xy, 1 zconv,
  * 2 pair_energy, 3 inv_yx, 4 accum, 5 exx_total, 6 to_float).

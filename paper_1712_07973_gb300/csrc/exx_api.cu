@@ -859,6 +859,19 @@ exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host
   return check_wait_flag(p, st);
 }
 
+exx_status_t exx_plan_set_lanes(exx_plan_t p, int lanes) {
+  if (p == nullptr || lanes < 1 || lanes > 2) return EXX_ERR_INVALID_ARG;
+  if (lanes == 2 && p->ls[0] == nullptr) return EXX_ERR_NOT_SUPPORTED;
+  p->lanes = lanes;
+  return EXX_OK;
+}
+
+exx_status_t exx_plan_get_lanes(exx_plan_t p, int* lanes) {
+  if (p == nullptr || lanes == nullptr) return EXX_ERR_INVALID_ARG;
+  *lanes = p->lanes;
+  return EXX_OK;
+}
+
 exx_status_t exx_profile_enable(exx_plan_t p, int enable) {
   if (p == nullptr) return EXX_ERR_INVALID_ARG;
   p->prof = enable != 0;

@@ -46,6 +46,8 @@ EXPORTS = {
     "exx_apply_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _c_double_p,
                                       ctypes.c_void_p]),
     "exx_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "exx_plan_set_lanes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "exx_plan_get_lanes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "exx_profile_read": (ctypes.c_int, [ctypes.c_void_p, _c_double_p,
                                         ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
     "exx_kernel_spectrum": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
@@ -269,6 +271,11 @@ class ExxPlan:
 
     KINDS = ("fwd_xy", "zconv", "pair_energy", "inv_yx", "accum", "exx_total", "to_float")
 
+    def set_lanes(self, lanes):
+        """1: every kernel on the caller's stream; 2: consecutive tiles on two
+        internal streams (the default where the plan has several tiles)."""
+        _check(self.lib.exx_plan_set_lanes(self.handle, int(lanes)), "exx_plan_set_lanes", self.handle)
+
     def profile(self, enable=True):
         _check(self.lib.exx_profile_enable(self.handle, int(bool(enable))), "exx_profile_enable")
 
@@ -290,8 +297,10 @@ class ExxPlan:
         _check(self.lib.exx_plan_info(self.handle, ctypes.byref(t), ctypes.byref(nt),
                                       ctypes.byref(ws), ctypes.byref(la), ctypes.byref(le)),
                "exx_plan_info")
+        lanes = ctypes.c_int()
+        _check(self.lib.exx_plan_get_lanes(self.handle, ctypes.byref(lanes)), "exx_plan_get_lanes")
         return {"tile": t.value, "ntiles": nt.value, "workspace_bytes": ws.value,
-                "launches_apply": la.value, "launches_energy": le.value}
+                "launches_apply": la.value, "launches_energy": le.value, "lanes": lanes.value}
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
