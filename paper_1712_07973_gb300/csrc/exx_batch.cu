@@ -137,6 +137,13 @@ struct exx_batch_s {
   bool have_vx = false;
   bool buffers_set = false;
   bool vec2 = true;  // every orbital array 8-byte aligned: paired loads in accum
+  // second pipeline lane (as in a single plan): its workspaces, streams, events
+  int lanes = 1;
+  double* epart2 = nullptr;
+  void* X_2 = nullptr;
+  void* V_2 = nullptr;
+  cudaStream_t ls[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_done[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // graph capture
   bool graph_on = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [apply, energy]
@@ -159,6 +166,14 @@ void batch_free(exx_batch_t b) {
   }
   for (int k = 0; k < 2; ++k)
     if (b->gexec[k]) cudaGraphExecDestroy(b->gexec[k]);
+  for (void* q : {static_cast<void*>(b->epart2), b->X_2, b->V_2})
+    if (q) cudaFree(q);
+  for (int l = 0; l < 2; ++l) {
+    if (b->ls[l]) cudaStreamDestroy(b->ls[l]);
+    if (b->ev_done[l]) cudaEventDestroy(b->ev_done[l]);
+    if (b->ev_free[l]) cudaEventDestroy(b->ev_free[l]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
 }
 
 template <typename T> bool balloc(exx_batch_t b, T** p, size_t bytes) {
@@ -178,33 +193,60 @@ exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, cudaStream_t st) 
     for (const Mol& m : b->mol) tot += (long long)m.N * m.n * m.n * m.n;
     if (cudaMemsetAsync(b->vacc, 0, (size_t)tot * sizeof(double), st) != cudaSuccess) return EXX_ERR_CUDA;
   }
+  // two lanes: consecutive waves alternate between two streams with their own
+  // workspaces; the accumulation stays on st in wave order
+  const int nl = b->lanes;
+  if (nl > 1) {
+    if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return EXX_ERR_CUDA;
+    for (int l = 0; l < nl; ++l)
+      if (cudaStreamWaitEvent(b->ls[l], b->ev_fork, 0) != cudaSuccess) return EXX_ERR_CUDA;
+  }
+  void* Xl[2] = {b->X, b->X_2};
+  void* Vl[2] = {b->V, b->V_2};
+  double* epl[2] = {b->epart, b->epart2};
+  bool used[2] = {false, false};
+  int k = 0;
   for (const Group& g : b->groups) {
     const long long n3 = (long long)g.n * g.n * g.n;
     const int nper = (g.n + 1) * g.ops->nyb;
     const double h3 = g.h * g.h * g.h;
     for (const Wave& w : g.waves) {
       const int4* pr = b->d_pairs + w.pair_off;
-      g.ops->fwd_xy(nullptr, reinterpret_cast<const void* const*>(b->d_psi_tab), pr, w.npair, b->X,
-                    g.tw, n3, st);
-      g.ops->zconv(b->X, g.Gs, g.tw, &g.gmap, b->epart, b->d_err, w.npair, !apply, st);
-      k_pair_energy<<<(w.npair * 32 + 255) / 256, 256, 0, st>>>(b->epart, nper, pr, w.npair, h3,
+      const int l = nl > 1 ? (k++ & 1) : 0;
+      cudaStream_t sl = nl > 1 ? b->ls[l] : st;
+      g.ops->fwd_xy(nullptr, reinterpret_cast<const void* const*>(b->d_psi_tab), pr, w.npair, Xl[l],
+                    g.tw, n3, sl);
+      g.ops->zconv(Xl[l], g.Gs, g.tw, &g.gmap, epl[l], b->d_err, w.npair, !apply, sl);
+      k_pair_energy<<<(w.npair * 32 + 255) / 256, 256, 0, sl>>>(epl[l], nper, pr, w.npair, h3,
                                                                  b->Epair);
       if (apply) {
-        g.ops->inv_yx(b->X, b->V, g.tw, w.npair, st);
+        if (nl > 1 && used[l] && cudaStreamWaitEvent(sl, b->ev_free[l], 0) != cudaSuccess)
+          return EXX_ERR_CUDA;
+        g.ops->inv_yx(Xl[l], Vl[l], g.tw, w.npair, sl);
+        if (nl > 1 && (cudaEventRecord(b->ev_done[l], sl) != cudaSuccess ||
+                       cudaStreamWaitEvent(st, b->ev_done[l], 0) != cudaSuccess))
+          return EXX_ERR_CUDA;
+        used[l] = true;
         const bool v2 = b->vec2 && (n3 % 2) == 0;
         const int threads = 256;
         const long long blocks = (n3 / (v2 ? 2 : 1) + threads - 1) / threads;
         if (v2)
           k_accum_batch<float, 8, 2><<<dim3((unsigned)blocks, w.ntile), threads, 0, st>>>(
-              b->d_psi_tab, static_cast<const float*>(b->V), b->d_vacc_tab, b->d_occ,
+              b->d_psi_tab, static_cast<const float*>(Vl[l]), b->d_vacc_tab, b->d_occ,
               b->d_tiles + w.tile_off, n3);
         else
           k_accum_batch<float, 8, 1><<<dim3((unsigned)blocks, w.ntile), threads, 0, st>>>(
-              b->d_psi_tab, static_cast<const float*>(b->V), b->d_vacc_tab, b->d_occ,
+              b->d_psi_tab, static_cast<const float*>(Vl[l]), b->d_vacc_tab, b->d_occ,
               b->d_tiles + w.tile_off, n3);
+        if (nl > 1 && cudaEventRecord(b->ev_free[l], st) != cudaSuccess) return EXX_ERR_CUDA;
       }
     }
   }
+  if (nl > 1)  // join both lanes
+    for (int l = 0; l < nl; ++l)
+      if (cudaEventRecord(b->ev_done[l], b->ls[l]) != cudaSuccess ||
+          cudaStreamWaitEvent(st, b->ev_done[l], 0) != cudaSuccess)
+        return EXX_ERR_CUDA;
   k_exx_total_batch<<<b->nmol, 256, 0, st>>>(b->Epair, b->d_mt, b->d_occ, E_dev);
   if (apply && b->have_vx) {
     long long mx = 0;
@@ -445,6 +487,26 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
     batch_free(b);
     delete b;
     return EXX_ERR_OOM;
+  }
+  {
+    size_t nwaves = 0;
+    for (const Group& g : b->groups) nwaves += g.waves.size();
+    const char* env = std::getenv("EXX_LANES");
+    b->lanes = (env && env[0] == '1') || nwaves < 2 ? 1 : 2;
+  }
+  if (b->lanes > 1) {
+    if (!balloc(b, &b->epart2, b->ep_bytes) || !balloc(b, &b->X_2, b->x_bytes) ||
+        !balloc(b, &b->V_2, b->v_bytes)) {
+      batch_free(b);
+      delete b;
+      return EXX_ERR_OOM;
+    }
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+      e = cudaStreamCreateWithFlags(&b->ls[l], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done[l], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_free[l], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 2 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

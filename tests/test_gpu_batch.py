@@ -176,3 +176,29 @@ def test_tuned_tile_gives_same_results(env, tmp_path, monkeypatch):
     assert torch.allclose(va, v0, rtol=0, atol=1e-12 * float(v0.abs().max()))
     p0.close()
     pa.close()
+
+
+def test_batch_two_lanes_equal_one_lane(env, monkeypatch):
+    # consecutive waves on two streams (the default) against one stream:
+    # identical results (the accumulation runs in wave order either way),
+    # eagerly and through the captured graph
+    torch, dev, exx = env
+    psis, occs, mols = _small(env)
+    pt = [torch.from_numpy(p).to(dev, torch.float32) for p in psis]
+    out = []
+    for lanes in ("1", "2"):
+        monkeypatch.setenv("EXX_LANES", lanes)
+        b = exx.ExxBatch(mols)
+        vx = [torch.empty_like(p) for p in pt]
+        b.set_buffers(pt, vx)
+        E = b.apply().cpu()
+        b.graph(True)
+        Eg = b.apply().cpu()
+        torch.cuda.synchronize()
+        assert torch.equal(E, Eg)
+        out.append((E, [v.cpu() for v in vx]))
+        b.close()
+    (E1, v1), (E2, v2) = out
+    assert torch.equal(E1, E2)
+    for a, c in zip(v1, v2):
+        assert torch.equal(a, c)
