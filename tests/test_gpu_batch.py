@@ -192,10 +192,13 @@ def test_batch_two_lanes_equal_one_lane(env, monkeypatch):
         vx = [torch.empty_like(p) for p in pt]
         b.set_buffers(pt, vx)
         E = b.apply().cpu()
-        b.graph(True)
-        Eg = b.apply().cpu()
-        torch.cuda.synchronize()
-        assert torch.equal(E, Eg)
+        b.graph(True)  # capture needs a created stream
+        s = torch.cuda.Stream()
+        Eg = torch.zeros(len(mols), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(s):
+            b.apply(Eg, stream=s)
+        s.synchronize()
+        assert torch.equal(E, Eg.cpu())
         out.append((E, [v.cpu() for v in vx]))
         b.close()
     (E1, v1), (E2, v2) = out
