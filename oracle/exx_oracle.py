@@ -24,7 +24,7 @@ What it computes (arXiv 1712.07973, Ratcliff et al.):
   symmetry V_ij = V_ji lets pair (i, j) serve both (Vx psi)_i and (Vx psi)_j
   (Sec. 2.1, round-robin paragraph).
 
-Readings where the paper is silent (each is also listed in the design doc):
+Readings where the paper is silent:
 
 * The paper names the interpolating-scaling-function Green's function but
   prints no formula for it.  This oracle uses the band-limited ("sinc basis")
