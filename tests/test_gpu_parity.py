@@ -524,3 +524,19 @@ def test_two_lane_pipeline_equals_one_lane(torch_dev, monkeypatch, prec):
     assert E1 == E2 and Ee1 == Ee2
     assert torch.equal(v1, v2)
     assert np.array_equal(P1, P2)
+
+
+@pytest.mark.parametrize("kernel,omega", [("hockney", 0.0), ("erfc", 0.3), ("periodic", 0.0),
+                                          ("slab", 0.0), ("wire", 0.0)])
+@pytest.mark.parametrize("n", [16, 32])
+def test_fp32_every_kernel_kind_against_fp64_oracle(torch_dev, kernel, omega, n):
+    # the FP32 path (gain-corrected forward transforms, FP64 reductions) for
+    # every kernel kind and boundary condition, 5 orbitals over a ragged tile
+    psi = _orbitals(n, 5, seed=200 + n, h=0.45)
+    occ = np.array([2.0, 1.0, 2.0, 0.5, 1.5])
+    E, Ee, vx, Eij = _gpu(torch_dev, psi, occ, 0.25, 0.45, "fp32", kernel=kernel, omega=omega)
+    okind = {"hockney": o.KERNEL_HOCKNEY, "erfc": o.KERNEL_ERFC}.get(kernel, kernel)
+    Eo, vxo, Eijo = _oracle(psi, occ, 0.25, 0.45, okind, omega=omega)
+    assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6, (E, Ee, Eo)
+    assert np.max(np.abs(Eij - Eijo)) <= 1e-6
+    assert np.max(np.abs(vx - vxo)) <= 2e-6 * np.max(np.abs(vxo))
