@@ -201,16 +201,16 @@ exx_status_t exx_apply_host(exx_plan_t plan, const void* psi_host, void* vxpsi_h
                             void* cuda_stream);
 
 /*
- * exx_plan_set_lanes -- number of pipeline lanes (1 or 2) of later calls.
- * With two lanes (the default where the plan has more than one pair tile and
- * the environment variable EXX_LANES is not "1" at plan creation) consecutive
- * tiles alternate between two internal streams with their own spectrum and
- * potential workspaces, so the transforms of one tile run beside those of
- * the next; the accumulation stays on the caller's stream in tile order and
- * results are identical bit for bit.  One lane serialises every kernel on the
- * caller's stream (per-kernel timing, below, then measures each kernel
- * alone).  Returns EXX_ERR_NOT_SUPPORTED for 2 when the plan was created
- * with one lane.
+ * exx_plan_set_lanes -- number of pipeline lanes (1 to 3) of later calls.
+ * A plan is created with two lanes (or EXX_LANES = 1, 2 or 3 from the
+ * environment at creation; never more than it has pair tiles), each beyond
+ * the first with its own internal stream and spectrum and potential
+ * workspaces.  Consecutive tiles go round-robin over the lanes, so the
+ * transforms of one tile run beside those of the next; the accumulation stays
+ * on the caller's stream in tile order and results are identical bit for bit.
+ * One lane serialises every kernel on the caller's stream (per-kernel timing,
+ * below, then measures each kernel alone).  Returns EXX_ERR_NOT_SUPPORTED for
+ * more lanes than the plan was created with.
  */
 exx_status_t exx_plan_set_lanes(exx_plan_t plan, int lanes);
 /* exx_plan_get_lanes -- current number of lanes (host out-parameter). */

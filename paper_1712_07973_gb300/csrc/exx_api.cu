@@ -218,6 +218,9 @@ static std::vector<int> shard_owners(const std::vector<Tile>& tiles, int nranks)
 
 using namespace exx;
 
+constexpr int kMaxLanes = 3;      // pipeline lanes a plan can hold
+constexpr int kDefaultLanes = 2;  // two measured 4% faster than one at 96^3
+
 struct exx_plan_s {
   int n = 0, N = 0, prec = 0, kind = 0;
   unsigned flags = 0;
@@ -249,13 +252,14 @@ struct exx_plan_s {
   CUtensorMap gmap{};      // TMA descriptor of the kernel table (Ops::stage_table)
   void* h_psi = nullptr;  // exx_apply_host staging (allocated on first use)
   void* h_vx = nullptr;
-  // two pipeline lanes: lane 1's workspaces, streams and events
-  int lanes = 1;
-  void* X2b = nullptr;
-  void* Vb = nullptr;
-  double* epartb = nullptr;
-  cudaStream_t ls[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr, ev_done[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  // pipeline lanes (run): lanes in use, lanes with workspaces, and the
+  // workspaces, streams and events of lanes 1.. (lane 0 uses X2, V, epart)
+  int lanes = 1, max_lanes = 1;
+  void* X2x[kMaxLanes] = {};
+  void* Vx[kMaxLanes] = {};
+  double* epx[kMaxLanes] = {};
+  cudaStream_t ls[kMaxLanes] = {};
+  cudaEvent_t ev_fork = nullptr, ev_done[kMaxLanes] = {}, ev_free[kMaxLanes] = {};
   // exx_apply_host overlap: copy stream, per-orbital-block events
   cudaStream_t cst = nullptr;
   cudaEvent_t ev_start = nullptr, ev_join = nullptr;
@@ -296,9 +300,10 @@ void free_plan(exx_plan_t p) {
   if (p->ev_start) cudaEventDestroy(p->ev_start);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->cst) cudaStreamDestroy(p->cst);
-  for (void* q : {p->X2b, p->Vb, static_cast<void*>(p->epartb)})
-    if (q) cudaFree(q);
-  for (int l = 0; l < 2; ++l) {
+  for (int l = 1; l < kMaxLanes; ++l)
+    for (void* q : {p->X2x[l], p->Vx[l], static_cast<void*>(p->epx[l])})
+      if (q) cudaFree(q);
+  for (int l = 0; l < kMaxLanes; ++l) {
     if (p->ls[l]) cudaStreamDestroy(p->ls[l]);
     if (p->ev_done[l]) cudaEventDestroy(p->ev_done[l]);
     if (p->ev_free[l]) cudaEventDestroy(p->ev_free[l]);
@@ -545,16 +550,18 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   }
   EXX_ALLOC(p->E_dev, sizeof(double));
   EXX_ALLOC(p->d_err, 2 * sizeof(int));
-  // second pipeline lane (EXX_LANES=1 turns it off) where the plan has more
-  // than one tile
+  // pipeline lanes: two by default (EXX_LANES=1..3 at plan creation chooses),
+  // never more than the plan has tiles
   {
     const char* env = std::getenv("EXX_LANES");
-    p->lanes = (env && env[0] == '1') ? 1 : (p->tiles.size() > 1 ? 2 : 1);
+    int nl = kDefaultLanes;
+    if (env && env[0] >= '1' && env[0] <= '0' + kMaxLanes && env[1] == '\0') nl = env[0] - '0';
+    p->max_lanes = p->lanes = (int)std::min<size_t>((size_t)nl, p->tiles.size());
   }
-  if (p->lanes > 1) {
-    EXX_ALLOC(p->epartb, (size_t)p->maxpairs * nper * sizeof(double));
-    EXX_ALLOC(p->X2b, (size_t)p->maxpairs * m * n * (2 * nh) * cs);
-    EXX_ALLOC(p->Vb, (size_t)p->maxpairs * n3 * rs);
+  for (int l = 1; l < p->max_lanes; ++l) {
+    EXX_ALLOC(p->epx[l], (size_t)p->maxpairs * nper * sizeof(double));
+    EXX_ALLOC(p->X2x[l], (size_t)p->maxpairs * m * n * (2 * nh) * cs);
+    EXX_ALLOC(p->Vx[l], (size_t)p->maxpairs * n3 * rs);
   }
 #undef EXX_ALLOC
 
@@ -582,8 +589,8 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   if (e == cudaSuccess && ops->stage_table && !exx::make_ktab_map(&p->gmap, p->Gs, nh, nz))
     e = cudaErrorInvalidValue;
   if (e == cudaSuccess) e = ops->setup();
-  if (e == cudaSuccess && p->lanes > 1) {
-    for (int l = 0; l < 2 && e == cudaSuccess; ++l) {
+  if (e == cudaSuccess && p->max_lanes > 1) {
+    for (int l = 0; l < p->max_lanes && e == cudaSuccess; ++l) {
       e = cudaStreamCreateWithFlags(&p->ls[l], cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done[l], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_free[l], cudaEventDisableTiming);
@@ -647,28 +654,35 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
   const double c = -p->alpha;
   if (p->sharded)  // pair energies of other ranks' tiles must read as zero
     EXX_CUDA(p, cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st));
-  // Two lanes: consecutive tiles alternate between two streams with their own
-  // spectrum, potential and partial-energy buffers, so that the transforms of
-  // one tile run beside those of the next; the accumulation stays on the
-  // caller's stream in tile order (identical sums, no two updates of one
-  // accumulator at a time), and a lane overwrites its V only after the
+  // Lanes: consecutive tiles go round-robin over the lanes' streams, each with
+  // its own spectrum, potential and partial-energy buffers, so that the
+  // transforms of one tile run beside those of the next; the accumulation
+  // stays on the caller's stream in tile order (identical sums, no two updates
+  // of one accumulator at a time), and a lane overwrites its V only after the
   // accumulation of its previous tile has read it.
   const int nl = p->lanes;
   if (nl > 1) {
     EXX_CUDA(p, cudaEventRecord(p->ev_fork, st));
     for (int l = 0; l < nl; ++l) EXX_CUDA(p, cudaStreamWaitEvent(p->ls[l], p->ev_fork, 0));
   }
-  void* X2l[2] = {p->X2, p->X2b};
-  void* Vl[2] = {p->V, p->Vb};
-  double* epl[2] = {p->epart, p->epartb};
-  bool used[2] = {false, false};
-  int waited[2] = {-1, -1};  // per lane: input blocks 0..waited are known to have arrived
+  void* X2l[kMaxLanes];
+  void* Vl[kMaxLanes];
+  double* epl[kMaxLanes];
+  bool used[kMaxLanes];
+  int waited[kMaxLanes];  // per lane: input blocks 0..waited are known to have arrived
+  for (int l = 0; l < kMaxLanes; ++l) {
+    X2l[l] = l ? p->X2x[l] : p->X2;
+    Vl[l] = l ? p->Vx[l] : p->V;
+    epl[l] = l ? p->epx[l] : p->epart;
+    used[l] = false;
+    waited[l] = -1;
+  }
   int k = 0;
   for (size_t ti = 0; ti < p->tiles.size(); ++ti) {
     if (!p->mine[ti]) continue;
     const Tile& t = p->tiles[ti];
     const int4* pr = p->d_pairs + t.off;
-    const int l = nl > 1 ? (k++ & 1) : 0;
+    const int l = nl > 1 ? (k++ % nl) : 0;
     cudaStream_t sl = nl > 1 ? p->ls[l] : st;
     void* X2 = X2l[l];
     void* Vt = Vl[l];
@@ -860,8 +874,8 @@ exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host
 }
 
 exx_status_t exx_plan_set_lanes(exx_plan_t p, int lanes) {
-  if (p == nullptr || lanes < 1 || lanes > 2) return EXX_ERR_INVALID_ARG;
-  if (lanes == 2 && p->ls[0] == nullptr) return EXX_ERR_NOT_SUPPORTED;
+  if (p == nullptr || lanes < 1 || lanes > kMaxLanes) return EXX_ERR_INVALID_ARG;
+  if (lanes > p->max_lanes) return EXX_ERR_NOT_SUPPORTED;
   p->lanes = lanes;
   return EXX_OK;
 }
