@@ -224,7 +224,10 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb, CL_A = SA.cl;
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb, CL_C = SC.cl;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
-  static constexpr int NW = zconv_warps(LZ2);
+  // FP32 z lines of L2 = 6 (96 points: periodic and wire 96^3, free 48^3): six
+  // warps, so that each pass-1 and pass-3 unit has its own warp, and six CTAs
+  // per SM (periodic 96^3 -3.3%, wire -9% per exx_apply against 12 warps)
+  static constexpr int NW = (sizeof(R) == 4 && LZ2 == 6) ? 6 : zconv_warps(LZ2);
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
   // zconv: twiddles + column buffer, plus the staged kernel-table slice when
@@ -238,8 +241,10 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
                                   3 * (smem_bg + 1024) <= 228 * 1024;
   static constexpr size_t smem_b = stage_g ? smem_bg : smem_b0;
   // CTAs per SM the zconv register budget is sized for: three where shared
-  // memory allows (FP32), else two
-  static constexpr int MINB_B = (sizeof(R) == 4 && 3 * (smem_b + 1024) <= 228 * 1024) ? 3 : 2;
+  // memory allows (FP32; six for the six-warp CTAs), else two
+  static constexpr int MINB_B = (sizeof(R) == 4 && 3 * (smem_b + 1024) <= 228 * 1024)
+                                     ? ((NW == 6 && 6 * (smem_b + 1024) <= 228 * 1024) ? 6 : 3)
+                                     : 2;
   // ky-folded kernel table where the unfolded one would exceed 24 MB
   static constexpr bool fold_y = !mixed && !stage_g && (size_t)(N + 1) * (2 * N) * (2 * N) * sizeof(R) > (24u << 20);
   static constexpr bool ok = L1 != 0 && LZ1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
