@@ -645,7 +645,6 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
   const long long n3 = (long long)n * n * n;
   const double h3 = p->h * p->h * p->h;
   const int nper = (p->ops->n + 1) * p->ops->nyb;
-  const size_t rs = p->prec == EXX_FP64 ? sizeof(double) : sizeof(float);
   double* acc = nullptr;
   if (apply) {
     acc = p->vacc ? p->vacc : static_cast<double*>(vxpsi);
@@ -759,7 +758,6 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
     if (blocks > 152 * 32) blocks = 152 * 32;
     k_to_float<<<(int)blocks, 256, 0, st>>>(p->vacc, static_cast<float*>(vxpsi), tot);
   }
-  (void)rs;
   EXX_CUDA(p, cudaGetLastError());
   return EXX_OK;
 }
