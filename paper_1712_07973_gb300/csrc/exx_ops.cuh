@@ -48,8 +48,9 @@ constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation 
 // Launch shape of the slab kernels (fwd_xy, inv_yx): shared memory = fixed
 // part (slab + twiddles) + y-pass scratch.  In order of preference:
 //   warp-owned y passes (q = 0, two scratch rows per warp) as four CTAs of
-//   160 threads per SM when asked for and they fit in a quarter of an SM
-//   (small slabs: periodic 96^3 -6.6% per exx_apply against two CTAs of 320),
+//   192 threads per SM when asked for and they fit in a quarter of an SM
+//   (small slabs: periodic 96^3 -6.6% per exx_apply against two CTAs of 320
+//   with 160 threads per CTA, a further -1.8% with 192),
 //   two CTAs of 320 when they fit in half an SM, else one CTA of 640;
 //   the same with the slab split over a two-CTA cluster (cl = 2, half the
 //   columns per CTA; fixed2 is its fixed part), when allowed, with 640 or
@@ -64,9 +65,11 @@ struct SlabShape {
   bool fits;
 };
 constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_t line,
-                               bool prefer_two) {
+                               bool prefer_two, bool fp32) {
   const size_t half = 113 * 1024;
-  if (prefer_two && fixed + 10 * line <= 56 * 1024)  // small slabs: four CTAs of 160
+  if (prefer_two && fp32 && fixed + 12 * line <= 56 * 1024)  // small slabs: four CTAs of 192
+    return SlabShape{0, 192, 4, 1, fixed + 12 * line, true};
+  if (prefer_two && fixed + 10 * line <= 56 * 1024)  // (FP64: 160, within the registers)
     return SlabShape{0, 160, 4, 1, fixed + 10 * line, true};
   if (prefer_two && fixed + 20 * line <= half) return SlabShape{0, 320, 2, 1, fixed + 20 * line, true};
   if (fixed + 40 * line <= kSmemPerCTA) return SlabShape{0, 640, 1, 1, fixed + 40 * line, true};
@@ -218,9 +221,11 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   static constexpr size_t slab2 = split_ok ? (size_t)slab_elems(N, G / 2) * sizeof(C) : 0;
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
   static constexpr SlabShape SA = slab_shape(slab + (size_t)(L + N) * sizeof(C),
-                                             slab2 + (size_t)(L + N) * sizeof(C), split_ok, line, true);
+                                             slab2 + (size_t)(L + N) * sizeof(C), split_ok, line,
+                                             true, sizeof(R) == 4);
   static constexpr SlabShape SC = slab_shape(slab + (size_t)2 * L * sizeof(C),
-                                             slab2 + (size_t)2 * L * sizeof(C), split_ok, line, true);
+                                             slab2 + (size_t)2 * L * sizeof(C), split_ok, line,
+                                             true, sizeof(R) == 4);
   static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb, CL_A = SA.cl;
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb, CL_C = SC.cl;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
