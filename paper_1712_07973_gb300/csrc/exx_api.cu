@@ -4,9 +4,13 @@
 // 1712.07973: Green's function on the mesh, applied by a zero-padded FFT),
 // the FFT twiddles, the pair-tile schedule over the N(N+1)/2 pairs (Sec. 2,
 // pair-count paragraph; Table pscount) and the device workspace of one tile.
-// exx_apply / exx_energy enqueue the tile pipeline on the caller's stream:
+// exx_apply / exx_energy enqueue the tile pipeline behind the caller's stream:
 //   fwd_xy -> zconv -> pair_energy [-> inv_yx -> accum]   per pair tile
 //   exx_total [-> convert]                                once
+// With two or three lanes the transforms of consecutive tiles run on the
+// lanes' internal streams (forked from and joined back into the caller's
+// stream through events); the accumulation stays on the caller's stream in
+// tile order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
