@@ -67,10 +67,13 @@ def dist_env():
 
 
 def kernel_source_hash():
+    """Hash of the kernel sources' code (line comments and blank lines left
+    out, so that a comment edit does not invalidate the committed counters)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1712_07973_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1712_07973_gb300", "csrc", f)) as fh:
+            code = [ln.split("//", 1)[0].strip() for ln in fh.read().splitlines()]
+        h.update("\n".join(ln for ln in code if ln).encode())
     return h.hexdigest()[:16]
 
 

@@ -23,7 +23,9 @@
 // Layouts: psi[o][z][y][x]; X[p][kx][z][ky] complex; V[p][z][y][x].
 // With periodic boundary conditions (template flag PER) the grid has 2n points
 // per axis, the lines are not padded and no transform is pruned; large slabs
-// are split over two-CTA clusters (CL = 2).
+// are split over two-CTA clusters (CL = 2).  Mixed boundary conditions give
+// zconv a z line of its own (NZ, PERZ): slab = periodic x, y with a free z;
+// wire = free x, y with a periodic z.
 #pragma once
 
 #include <cooperative_groups.h>

@@ -1,6 +1,6 @@
-// Per-grid-size launch table of the pair pipeline.  One OpsImpl<R, N> is
-// instantiated per supported (precision, n) in the exx_inst_*.cu files; the
-// C-ABI layer picks the table at plan creation.
+// Per-grid-size launch table of the pair pipeline.  One OpsImpl<R, N, ...> is
+// instantiated per supported (precision, n, boundary conditions) in the
+// exx_inst_*.cu files; the C-ABI layer picks the table at plan creation.
 #pragma once
 
 #include <cmath>
