@@ -232,7 +232,11 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   // FP32 z lines of L2 = 6 (96 points: periodic and wire 96^3, free 48^3): six
   // warps, so that each pass-1 and pass-3 unit has its own warp, and six CTAs
   // per SM (periodic 96^3 -3.3%, wire -9% per exx_apply against 12 warps)
-  static constexpr int NW = (sizeof(R) == 4 && LZ2 == 6) ? 6 : zconv_warps(LZ2);
+  // (FP32 L2 = 14, 224-point lines: eight warps, two rounds in every pass,
+  // rather than seven with three rounds in the second)
+  static constexpr int NW = (sizeof(R) == 4 && LZ2 == 6)    ? 6
+                            : (sizeof(R) == 4 && LZ2 == 14) ? 8
+                                                            : zconv_warps(LZ2);
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
   // zconv: twiddles + column buffer, plus the staged kernel-table slice when
@@ -245,11 +249,10 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
                                   (L * sizeof(R)) % 16 == 0 && LZ <= 256 &&
                                   3 * (smem_bg + 1024) <= 228 * 1024;
   static constexpr size_t smem_b = stage_g ? smem_bg : smem_b0;
-  // CTAs per SM the zconv register budget is sized for: three where shared
-  // memory allows (FP32; six for the six-warp CTAs), else two
-  static constexpr int MINB_B = (sizeof(R) == 4 && 3 * (smem_b + 1024) <= 228 * 1024)
-                                     ? ((NW == 6 && 6 * (smem_b + 1024) <= 228 * 1024) ? 6 : 3)
-                                     : 2;
+  // CTAs per SM the zconv register budget is sized for (FP32): as many as
+  // shared memory allows, at least three and at most eight; else two
+  static constexpr int CTAS_B = (int)((228 * 1024) / (smem_b + 1024));
+  static constexpr int MINB_B = (sizeof(R) == 4 && CTAS_B >= 3) ? (CTAS_B < 8 ? CTAS_B : 8) : 2;
   // ky-folded kernel table where the unfolded one would exceed 24 MB
   static constexpr bool fold_y = !mixed && !stage_g && (size_t)(N + 1) * (2 * N) * (2 * N) * sizeof(R) > (24u << 20);
   static constexpr bool ok = L1 != 0 && LZ1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
