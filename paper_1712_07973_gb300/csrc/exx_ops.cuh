@@ -233,9 +233,13 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   // warps, so that each pass-1 and pass-3 unit has its own warp, and six CTAs
   // per SM (periodic 96^3 -3.3%, wire -9% per exx_apply against 12 warps)
   // (FP32 L2 = 14, 224-point lines: eight warps, two rounds in every pass,
-  // rather than seven with three rounds in the second)
+  // rather than seven with three rounds in the second; FP32 L2 = 12,
+  // 192-point lines: eight warps with the kernel table read from L2, four
+  // CTAs per SM, -2.3% zconv at 96^3 against twelve warps with the staged
+  // table at three CTAs)
   static constexpr int NW = (sizeof(R) == 4 && LZ2 == 6)    ? 6
                             : (sizeof(R) == 4 && LZ2 == 14) ? 8
+                            : (sizeof(R) == 4 && LZ2 == 12) ? 8
                                                             : zconv_warps(LZ2);
   static constexpr int W = L < 32 ? L : 32;
   static constexpr int NYB = (L + W - 1) / W;
@@ -245,7 +249,7 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   static constexpr size_t smem_b0 = ((size_t)LZ + (size_t)LZ * W) * sizeof(C);
   static constexpr size_t smem_g = (size_t)LZ * W * sizeof(R);
   static constexpr size_t smem_bg = zconv_gsm_offset(LZ, W, sizeof(C)) + smem_g + 128;  // + alignment slack
-  static constexpr bool stage_g = sizeof(R) == 4 && (W * sizeof(R)) % 16 == 0 &&
+  static constexpr bool stage_g = sizeof(R) == 4 && LZ2 != 12 && (W * sizeof(R)) % 16 == 0 &&
                                   (L * sizeof(R)) % 16 == 0 && LZ <= 256 &&
                                   3 * (smem_bg + 1024) <= 228 * 1024;
   static constexpr size_t smem_b = stage_g ? smem_bg : smem_b0;
