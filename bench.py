@@ -21,7 +21,6 @@ implementation of this path to run) and prints the same JSON line.
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
