@@ -3,7 +3,8 @@
  *
  * The library applies the exact-exchange (Fock) operator of hybrid density
  * functionals to N real orbitals sampled on a uniform cubic grid with free
- * (isolated) boundary conditions, following arXiv 1712.07973 (Ratcliff et al.):
+ * (isolated) boundary conditions -- or, by kernel kind, periodic, slab or wire
+ * cells -- following arXiv 1712.07973 (Ratcliff et al.):
  *
  *   rho_ij(r)  = psi_i(r) psi_j(r)                       (Sec. 2.1, kernel 1)
  *   V_ij       = G * rho_ij, the free-BC Poisson solution (Sec. 2.1.2, kernel 2;
@@ -25,7 +26,10 @@
  *   device; "host" pointers are ordinary host memory.  The caller keeps
  *   ownership of every pointer it passes; the plan owns only what it allocates.
  * - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
- *   stream).  Work is enqueued on that stream.
+ *   stream).  Work is enqueued on that stream; a plan with several pipeline
+ *   lanes (exx_plan_set_lanes) forks onto internal streams after the work
+ *   already on it and joins back before the call's last step, so the
+ *   caller's stream order holds as if everything ran on it.
  * - Every entry point returns an exx_status_t and never aborts the process.
  *   On EXX_ERR_CUDA the CUDA error string is kept in the plan and returned by
  *   exx_last_error().
@@ -112,7 +116,7 @@ typedef enum {
  *   cuda_stream  stream for the plan's set-up uploads (synchronised on return).
  * The FP64 kernel spectrum is built on the host (Sec. 2.1.2 reading: the
  * Green's function discretised on the mesh), uploaded once, and workspaces for
- * one pair tile are allocated with cudaMalloc.
+ * one pair tile per pipeline lane are allocated with cudaMalloc.
  */
 exx_status_t exx_plan_create(exx_plan_t* out, const int grid[3], const double h[3],
                              double alpha, const double* occupations, int norb,
