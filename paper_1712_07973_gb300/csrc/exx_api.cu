@@ -223,7 +223,7 @@ static std::vector<int> shard_owners(const std::vector<Tile>& tiles, int nranks)
 using namespace exx;
 
 constexpr int kMaxLanes = 3;      // pipeline lanes a plan can hold
-constexpr int kDefaultLanes = 2;  // two measured 4% faster than one at 96^3
+constexpr int kDefaultLanes = 2;  // two measured 4% faster than one at 96^3 (unclustered slabs)
 
 struct exx_plan_s {
   int n = 0, N = 0, prec = 0, kind = 0;
@@ -554,11 +554,13 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   }
   EXX_ALLOC(p->E_dev, sizeof(double));
   EXX_ALLOC(p->d_err, 2 * sizeof(int));
-  // pipeline lanes: two by default (EXX_LANES=1..3 at plan creation chooses),
-  // never more than the plan has tiles
+  // pipeline lanes: two by default, one where the slab kernels run as two-CTA
+  // clusters (512 orbitals on 160^3: 17.5 s per step with one lane, 18.2 s
+  // with two); EXX_LANES=1..3 at plan creation chooses; never more than the
+  // plan has tiles
   {
     const char* env = std::getenv("EXX_LANES");
-    int nl = kDefaultLanes;
+    int nl = ops->clustered ? 1 : kDefaultLanes;
     if (env && env[0] >= '1' && env[0] <= '0' + kMaxLanes && env[1] == '\0') nl = env[0] - '0';
     p->max_lanes = p->lanes = (int)std::min<size_t>((size_t)nl, p->tiles.size());
   }

@@ -30,6 +30,7 @@ struct Ops {
   // gy[2n], gz[2nz]
   void (*gains)(double* gx, double* gy, double* gz) = nullptr;
   bool table_fold_y = false;  // kernel-table layout (build_kernel_table)
+  bool clustered = false;     // slab kernels launched as two-CTA clusters
   // psi_tab (device array of orbital-array pointers, indexed by the pair's
   // molecule slot) may be null, in which case every pair reads psi
   void (*fwd_xy)(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
@@ -335,6 +336,7 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
     o.smem_c = smem_c;
     o.setup = &setup;
     o.table_fold_y = fold_y;
+    o.clustered = CL_A > 1 || CL_C > 1;
     o.stage_table = stage_g;
     if constexpr (ok && sizeof(R) == 4) o.gains = &gains;
     o.fwd_xy = &fwd_xy;
