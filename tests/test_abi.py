@@ -161,3 +161,16 @@ def test_slab_and_wire_need_even_supported_grid(lib):
         assert lib.exx_kernel_spectrum(3, 0.4, kernel, 0.0,
                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
     assert _create(lib, kernel=6)[0] == 1
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    # the product path fails loudly where CUDA is missing: there is no host
+    # implementation behind the binding (this container has no GPU)
+    import torch
+    from paper_1712_07973_gb300 import exx
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(exx.ExxError, match="no CUDA device"):
+        exx.ExxPlan(8, 0.4, 0.25, [2.0, 2.0], precision="fp32")
+    with pytest.raises(exx.ExxError, match="no CUDA device"):
+        exx.ExxBatch([{"n": 8, "h": 0.4, "alpha": 0.25, "occupations": [2.0]}])
