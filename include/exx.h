@@ -79,7 +79,7 @@ typedef enum {
                              n h (the paper's own runs, Sec. 3, are periodic):
                              V_hat = 4 pi rho_hat / |k|^2 with k = 0 removed, no
                              padding; n even, n in {8,12,16,24,32,48,64,96,128,
-                             192} (FP64 up to 128)                                */
+                             192}                                                 */
   EXX_KERNEL_SLAB = 4,    /* slab ("surface") boundary conditions (Sec. 2.1.2:
                              other boundary conditions change only the Green's
                              function): x and y periodic with the cell n h, z

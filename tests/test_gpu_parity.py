@@ -340,7 +340,7 @@ def test_periodic_fp64(torch_dev, n):
                  _oracle(psi, occ, 0.25, 0.5, "periodic"))
 
 
-@pytest.mark.parametrize("n,prec", [(64, "fp32"), (96, "fp32"), (128, "fp64")])
+@pytest.mark.parametrize("n,prec", [(64, "fp32"), (96, "fp32"), (128, "fp64"), (192, "fp64")])
 def test_periodic_larger_grids(torch_dev, n, prec):
     psi = _orbitals(n, 3, seed=90 + n, h=0.4)
     occ = np.full(3, 2.0)
