@@ -43,10 +43,11 @@ template <> struct cvec<F32c> { using type = F32c2; };
 template <> struct creal<F32c2> { using type = F32c; };
 
 // PER: periodic boundary conditions (full lines of 2N points, nothing pruned);
-// otherwise free (lines of N points padded to 2N).
-template <int N, bool PER = false> struct GainModel {
-  using R = F32c;
-  using C = F32c2;
+// otherwise free (lines of N points padded to 2N).  S: the model's scalar
+// (F32c; a type with the same interface that does not round gives |d|^2 = 1).
+template <int N, bool PER = false, typename S = F32c> struct GainModel {
+  using R = S;
+  using C = typename cvec<S>::type;
   static constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   static constexpr int X1 = split_x(N), X2 = N / X1;
   static constexpr int G = PER ? L : N;  // input samples per line
@@ -59,7 +60,7 @@ template <int N, bool PER = false> struct GainModel {
     const double a = -M_PI * (double)(e % L) / (double)N;
     return mkc<C>(R(std::cos(a)), R(std::sin(a)));
   }
-  static C raw(double a, double b) { return mkc<C>(R(a, R::Raw{}), R(b, R::Raw{})); }
+  static C raw(double a, double b) { return mkc<C>(R(a, typename R::Raw{}), R(b, typename R::Raw{})); }
 
   // forward line transform of the y and z passes: in[n], n < G -> out[k]
   static void line(const C* in, C* out) {
