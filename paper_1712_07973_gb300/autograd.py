@@ -23,6 +23,15 @@ __all__ = ["ExxEnergy", "exx_energy"]
 
 
 class ExxEnergy(torch.autograd.Function):
+    """E_x(psi) with its gradient dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k.
+
+    forward: exx_apply when a gradient will be needed (the action is kept for
+    the backward), exx_energy otherwise or with recompute=True (the backward
+    then runs exx_apply again).  backward: the library's exchange action
+    times the per-orbital factor 2 f_k h^3 grad_out (one elementwise product
+    on the returned tensor; every pair solve runs in the library).
+    """
+
     @staticmethod
     def forward(ctx, psi, plan, recompute=False):
         if not isinstance(plan, ExxPlan):

@@ -81,6 +81,9 @@ _LIB = None
 
 
 class ExxError(RuntimeError):
+    """A non-zero exx_status_t from the library (``status``), with the call
+    that returned it and, where the plan kept one, the CUDA error text."""
+
     def __init__(self, status, where, detail=""):
         name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
         super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
@@ -225,12 +228,17 @@ class ExxPlan:
         return ctypes.c_void_p(psi.data_ptr())
 
     def energy(self, psi, stream=None):
+        """E_x of psi ([norb, n, n, n] CUDA tensor of the plan's dtype), in
+        hartree (exx_energy; synchronises the stream)."""
         E = ctypes.c_double()
         _check(self.lib.exx_energy(self.handle, self._psi(psi), ctypes.byref(E), _stream_ptr(stream)),
                "exx_energy", self.handle)
         return E.value
 
     def apply(self, psi, out=None, stream=None):
+        """(E_x, Vx psi): the energy and the exchange action for every orbital
+        (exx_apply).  out, if given, receives Vx psi (contiguous, psi's shape,
+        the plan's output dtype)."""
         import torch
         p = self._psi(psi)
         if out is None:
@@ -243,18 +251,23 @@ class ExxPlan:
         return E.value, out
 
     def apply_async(self, psi, out, E_dev=None, stream=None):
+        """exx_apply without synchronising: Vx psi into out and, if given, E_x
+        into the one-element FP64 device tensor E_dev (graph-capturable)."""
         p = self._psi(psi)
         e = ctypes.c_void_p(E_dev.data_ptr()) if E_dev is not None else ctypes.c_void_p()
         _check(self.lib.exx_apply_async(self.handle, p, ctypes.c_void_p(out.data_ptr()), e,
                                         _stream_ptr(stream)), "exx_apply_async", self.handle)
 
     def energy_async(self, psi, E_dev=None, stream=None):
+        """exx_energy without synchronising, E_x into E_dev (device)."""
         p = self._psi(psi)
         e = ctypes.c_void_p(E_dev.data_ptr()) if E_dev is not None else ctypes.c_void_p()
         _check(self.lib.exx_energy_async(self.handle, p, e, _stream_ptr(stream)),
                "exx_energy_async", self.handle)
 
     def pair_energies(self, stream=None):
+        """E_ij = h^3 sum rho_ij V_ij of the last call, pairs (0,0), (0,1), ..,
+        (N-1, N-1) in row-major order over i <= j (NumPy, FP64)."""
         P = self.norb * (self.norb + 1) // 2
         out = np.zeros(P, dtype=np.float64)
         _check(self.lib.exx_pair_energies(self.handle, out.ctypes.data_as(_c_double_p),
@@ -277,6 +290,8 @@ class ExxPlan:
         _check(self.lib.exx_plan_set_lanes(self.handle, int(lanes)), "exx_plan_set_lanes", self.handle)
 
     def profile(self, enable=True):
+        """Record CUDA events around every launch of later calls (per kernel
+        kind; read with profile_read)."""
         _check(self.lib.exx_profile_enable(self.handle, int(bool(enable))), "exx_profile_enable")
 
     def profile_read(self, reset=True):
@@ -292,6 +307,8 @@ class ExxPlan:
         _check(self.lib.exx_plan_set_shard(self.handle, int(rank), int(nranks)), "exx_plan_set_shard")
 
     def info(self):
+        """Tile edge, tile count, device workspace bytes, kernel launches per
+        apply / energy call and pipeline lanes of the plan."""
         t, nt, la, le = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ws = ctypes.c_size_t()
         _check(self.lib.exx_plan_info(self.handle, ctypes.byref(t), ctypes.byref(nt),
@@ -303,6 +320,7 @@ class ExxPlan:
                 "launches_apply": la.value, "launches_energy": le.value, "lanes": lanes.value}
 
     def close(self):
+        """Free the plan's device memory (exx_plan_destroy); idempotent."""
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.exx_plan_destroy(self.handle)
             self.handle = None
@@ -355,6 +373,8 @@ class ExxBatch:
         self._bound = None
 
     def set_buffers(self, psis, vxs=None, stream=None):
+        """Bind each molecule's orbitals (and Vx psi outputs) as contiguous
+        CUDA float32 tensors; rebinding keeps a captured graph valid."""
         import torch
         for k, (p, m) in enumerate(zip(psis, self.mols)):
             n = int(m["n"])
@@ -374,6 +394,8 @@ class ExxBatch:
         self._bound = (list(psis), list(vxs) if vxs is not None else None)
 
     def apply(self, E_dev=None, stream=None):
+        """E_x per molecule (FP64 device tensor) and Vx psi into the bound
+        outputs, asynchronously on the stream."""
         import torch
         if E_dev is None:
             E_dev = torch.zeros(self.nmol, dtype=torch.float64, device="cuda")
@@ -382,6 +404,7 @@ class ExxBatch:
         return E_dev
 
     def energy(self, E_dev=None, stream=None):
+        """E_x per molecule only (FP64 device tensor), asynchronously."""
         import torch
         if E_dev is None:
             E_dev = torch.zeros(self.nmol, dtype=torch.float64, device="cuda")
@@ -390,9 +413,12 @@ class ExxBatch:
         return E_dev
 
     def graph(self, enable=True):
+        """Capture each call kind once into a CUDA graph and replay it (needs a
+        created, non-default stream)."""
         _check(self.lib.exx_batch_graph(self.handle, int(bool(enable))), "exx_batch_graph")
 
     def pair_energies(self, mol, stream=None):
+        """E_ij of molecule ``mol`` from the last call (as ExxPlan.pair_energies)."""
         N = self._occ[mol].size
         out = np.zeros(N * (N + 1) // 2)
         _check(self.lib.exx_batch_pair_energies(self.handle, int(mol), out.ctypes.data_as(_c_double_p),
@@ -400,6 +426,8 @@ class ExxBatch:
         return out
 
     def info(self):
+        """Groups of equal (n, h), waves, workspace bytes, launches per apply
+        and total pairs of the batch."""
         g, w, la = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ws, pr = ctypes.c_size_t(), ctypes.c_longlong()
         _check(self.lib.exx_batch_info(self.handle, ctypes.byref(g), ctypes.byref(w), ctypes.byref(ws),
@@ -408,6 +436,7 @@ class ExxBatch:
                 "launches_apply": la.value, "pairs": pr.value}
 
     def close(self):
+        """Free the batch's device memory (exx_batch_destroy); idempotent."""
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.exx_batch_destroy(self.handle)
             self.handle = None
