@@ -1,27 +1,41 @@
 #!/usr/bin/env python
-"""Benchmark of the exact-exchange operator on one GB300 (or N replicas).
+"""Benchmark of the exact-exchange operator on one GB300 (or N GPUs, sharded).
 
-Workload (one "step" = one exx_apply: E_x plus the exchange action Vx psi,
-i.e. E_x and its gradient): 64 Lowdin-orthonormal Gaussian-combination
-orbitals on a 96^3 grid (192^3 zero-padded Poisson grid), h = 0.4 bohr,
-f = 2, alpha = 0.25, FP32 FFTs and products with FP64 kernel, E_x and Vx psi
-accumulation: 2080 pair solves per step.  Inputs are seeded synthetic
-orbitals (no dataset exists for this path), resident in HBM before timing.
+Workload (one "step" = one E_x + gradient: exx_gradient, i.e. E_x and
+dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k from all pair solves): 512
+Lowdin-orthonormal Gaussian-combination orbitals of a 256-site cluster on a
+160^3 grid (320^3 zero-padded Poisson grid), h = 0.42 bohr, f = 2,
+alpha = 0.25, FP32 FFTs and products with FP64 kernel, E_x and gradient
+accumulation: 131,328 pair solves per step (the pair count of the 512-orbital
+H2O row of the paper's Table pscount).  Inputs are seeded synthetic orbitals
+(no dataset exists for this path), resident in HBM before timing.
 
 Output: one JSON line (rank 0).  ``value`` is pair-solves/s over all ranks;
-``roofline`` describes the dominant kernel (per-kernel CUDA events on the
-launching stream over the timed region); ``e2e`` is the same metric through
-exx_apply_host with pinned host buffers; ``cpu_baseline`` is the FP64 NumPy
-oracle on the host cores over a bounded sample of the same pair solves.
+``roofline`` describes the dominant kernel (CUDA events recorded by the library
+on the launching stream around every launch of the timed region); ``e2e`` is
+the same metric through exx_gradient_host with pinned host buffers;
+``cpu_baseline`` is the FP64 NumPy oracle on the host cores over a bounded
+sample of the same pair solves, whose energies also give the FP32 path's
+per-pair error.  Sub-records: ``fp32_vs_fp64`` (the metric's FP32-vs-FP64
+comparison per E_x + gradient on the 128-orbital 128^3 workload, the largest
+whose FP64 step fits the run), ``c2`` (64 orbitals on 96^3) and ``batched``
+(the 16-molecule uneven batch and a 64-molecule small-molecule batch, FP32
+batched autograd against FP64 plain).
 
-``--impl reference`` times that oracle alone (there is no other
-implementation of this path to run) and prints the same JSON line.
+Under torchrun (N > 1 ranks, one GPU each) the step is the sharded path: each
+rank solves its share of the pair tiles and the partial E_x and gradients are
+summed with NCCL all-reduces (strong scaling: the work per step is fixed).
+
+``--impl reference`` times the FP64 oracle alone (there is no other
+implementation of this path to run) on a bounded sample of the same workload's
+pair solves per step and prints the same JSON line.
 """
 
 import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,26 +44,29 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "c2_fp32_n96_N64"
-METRIC = "EXX pair-solves/s (exx_apply: E_x + Vx psi gradient, FP32 FFTs, FP64 reductions)"
+WORKLOAD = "c5_large_n160_N512"
+METRIC = "EXX pair-solves/s and ms per E_x+gradient: FP32 batched vs FP64 plain at ≤1e-6 Ha"
 UNIT = "pair-solves/s"
 KERNEL_SOURCES = ["exx_fft.cuh", "exx_kernels.cuh", "exx_ops.cuh"]
+WORKLOADS = ["c5_large_n160_N512", "c3_grad_n128_N128", "c2_fp32_n96_N64"]
 
 
 def args_parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sample", type=int, default=128, help="pair solves timed on the CPU")
+    ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS,
+                    help="orbital workload of the timed step (default: 512 orbitals on 160^3)")
+    ap.add_argument("--cpu-sample", type=int, default=64,
+                    help="pair solves of the oracle sample (CPU baseline and per-pair errors)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD,
-                    choices=["c2_fp32_n96_N64", "c3_grad_n128_N128", "c5_large_n160_N512"],
-                    help="orbital workload of the timed step (default: 64 orbitals on 96^3)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP32-vs-FP64 sub-record")
+    ap.add_argument("--no-c2", action="store_true", help="skip the 64-orbital 96^3 sub-record")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
-                    help="also time the 16-molecule batched workload (one graph launch)")
+                    help="batched sub-records (16 uneven molecules; 64 small molecules)")
     ap.add_argument("--bc", choices=["free", "periodic", "slab", "wire"], default="free",
                     help="boundary conditions: free (zero-padded 2n FFTs), periodic cell, slab "
                          "(x, y periodic, z free) or wire (x, y free, z periodic)")
@@ -83,6 +100,25 @@ def measured_peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 # ------------------------------------------------------------- clocks
@@ -159,7 +195,7 @@ def half_lines(n, bc):
 
 
 def algorithmic_bytes(n, N, T, rs=4, bc="free"):
-    """Minimal HBM bytes of each kernel kind over one exx_apply.
+    """Minimal HBM bytes of each kernel kind over one step.
 
     x and y transforms of length 2h, z transforms of length 2hz (half_lines).
     Per pair: fwd_xy writes the y-transformed spectrum X2 ((h+1) n 2h complex);
@@ -182,7 +218,7 @@ def algorithmic_bytes(n, N, T, rs=4, bc="free"):
     return tot
 
 
-def committed_traffic(kernel):
+def committed_traffic(kernel, workload=WORKLOAD):
     """ncu DRAM bytes per launch from profiles/traffic.json, if the kernel
     sources are unchanged since the capture; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -190,114 +226,306 @@ def committed_traffic(kernel):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    e = d.get(WORKLOAD, {}).get(kernel)
+    e = d.get(workload, {}).get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------------ CPU oracle
-def cpu_oracle_rate(psi, r, npairs, seed=0, bc="free"):
-    """Time the FP64 oracle on a seeded sample of the workload's pair solves
-    (co-density, FFT Poisson solve, E_ij, both V psi products)."""
+def oracle_spectrum(n, h, bc="free"):
+    from oracle import exx_oracle as o
+    return {"periodic": lambda: o.kernel_spectrum_periodic(n, h),
+            "slab": lambda: o.kernel_spectrum_slab(n, h),
+            "wire": lambda: o.kernel_spectrum_wire(n, h),
+            "free": lambda: o.kernel_spectrum(o.kernel_real_space(n, h))}[bc]()
+
+
+def oracle_pairs(orb, pairs, r, Gh):
+    """Time the FP64 oracle on the given pair solves (co-density, FFT Poisson
+    solve, E_ij, both V psi products).  orb(i) returns orbital i as FP64
+    NumPy.  Returns (seconds, {(i, j): E_ij})."""
     import numpy as np
     from oracle import exx_oracle as o
-    Gh = {"periodic": lambda: o.kernel_spectrum_periodic(r.n, r.h),
-          "slab": lambda: o.kernel_spectrum_slab(r.n, r.h),
-          "wire": lambda: o.kernel_spectrum_wire(r.n, r.h),
-          "free": lambda: o.kernel_spectrum(o.kernel_real_space(r.n, r.h))}[bc]()
-    rng = np.random.default_rng(seed)
-    pairs = o.pair_list(r.norb)
-    pick = [pairs[k] for k in rng.choice(len(pairs), size=npairs, replace=False)]
-    acc = np.zeros((2,) + psi.shape[1:])
+    cache = {}
+
+    def get(i):
+        if i not in cache:
+            cache[i] = orb(i)
+        return cache[i]
+
+    for i, j in pairs:  # inputs ready before the clock starts
+        get(i), get(j)
+    acc = np.zeros((2,) + cache[pairs[0][0]].shape)
+    E = {}
     t0 = time.perf_counter()
-    for i, j in pick:
-        V, e = o.exx_pair(psi[i], psi[j], Gh, r.h)
-        acc[0] += (-r.alpha * r.occupation) * V * psi[j]
-        acc[1] += (-r.alpha * r.occupation) * V * psi[i]
-    dt = time.perf_counter() - t0
-    return npairs / dt, dt
+    for i, j in pairs:
+        V, e = o.exx_pair(get(i), get(j), Gh, r.h)
+        acc[0] += (-r.alpha * r.occupation) * V * get(j)
+        acc[1] += (-r.alpha * r.occupation) * V * get(i)
+        E[(i, j)] = e
+    return time.perf_counter() - t0, E
 
 
-def batched_line(torch, dev, exx, synth, stream):
-    """16 molecules of uneven size (N_m in [8, 96], n_m in {48..128}^3), FP32,
-    one CUDA-graph launch per step; compared with one plan per molecule."""
+def sample_pairs(N, count, seed):
     import numpy as np
-    recipes = synth.batched_workload()
+    P = N * (N + 1) // 2
+    rng = np.random.default_rng(seed)
+    g = np.sort(rng.choice(P, size=min(count, P), replace=False))
+    out = []
+    for gid in g:  # row-major decode over i <= j
+        i, rem = 0, int(gid)
+        while rem >= N - i:
+            rem -= N - i
+            i += 1
+        out.append((i, i + rem, int(gid)))
+    return out
+
+
+# ------------------------------------------------------------ timing helpers
+def cuda_time(torch, stream, fn, steps):
+    """Milliseconds per call of fn over steps calls (CUDA events on stream)."""
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def roofline_of(prof, alg, steps_timed, peak, peak_kind, workload, timed_region):
+    """Roofline object of the kernel kind with the largest measured time."""
+    dom = max(alg, key=lambda k: prof[k][0])
+    kms, kcnt = prof[dom]
+    per_launch_bytes = alg[dom] / (kcnt / steps_timed)
+    achieved = per_launch_bytes / (kms / kcnt * 1e-3) / 1e9
+    tot = sum(x[0] for x in prof.values())
+    shares = {k: round(v[0] / max(1e-9, tot), 4) for k, v in prof.items()}
+    per_kernel = {}
+    for k in alg:
+        ms_k, c_k = prof[k]
+        if c_k:
+            b = alg[k] / (c_k / steps_timed)
+            per_kernel[k] = {"avg_launch_ms": ms_k / c_k, "algorithmic_bytes_per_launch": int(b),
+                             "achieved_gbs": round(b / (ms_k / c_k * 1e-3) / 1e9, 1),
+                             "frac": round(b / (ms_k / c_k * 1e-3) / 1e9 / peak, 4)}
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": committed_traffic(dom, workload),
+            "algorithmic_bytes_per_launch": int(per_launch_bytes),
+            "avg_launch_ms": kms / kcnt, "kernel_shares": shares, "per_kernel": per_kernel,
+            "timed_region": timed_region}
+
+
+# ------------------------------------------------------------ sub-records
+def c2_record(torch, dev, exx, synth, stream, steps):
+    """64 orbitals on 96^3 (two pipeline lanes): throughput, roofline of the
+    serialised kernels, E_x error against the stored oracle value."""
+    import numpy as np
+    r, psi_np = synth.workload("c2_fp32_n96_N64")
+    psi = torch.from_numpy(psi_np).to(dev, torch.float32)
+    P = r.norb * (r.norb + 1) // 2
+    plan = exx.ExxPlan(r.n, r.h, r.alpha, np.full(r.norb, r.occupation), precision="fp32")
+    info = plan.info()
+    out = torch.empty_like(psi)
+    E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        plan.gradient_async(psi, out, E_dev)
+    ms = cuda_time(torch, stream, lambda: plan.gradient_async(psi, out, E_dev), steps)
+    E = float(E_dev.item())
+    plan.set_lanes(1)
+    plan.gradient_async(psi, out, E_dev)
+    plan.profile(True)
+    plan.profile_read(reset=True)
+    ms1 = cuda_time(torch, stream, lambda: plan.gradient_async(psi, out, E_dev), steps)
+    prof = plan.profile_read(reset=True)
+    plan.profile(False)
+    plan.close()
+    peak, kind = measured_peaks()
+    rl = roofline_of(prof, algorithmic_bytes(r.n, r.norb, info["tile"]), steps, peak, kind,
+                     "c2_fp32_n96_N64", f"{steps} steps, one pipeline lane, events around every launch")
+    rl["serialised_ms_per_step"] = ms1
+    rec = {"workload": "c2_fp32_n96_N64: 64 orbitals on 96^3 (192^3 padded), h = 0.4",
+           "pairs": P, "ms_per_step": ms, "value": P / (ms * 1e-3), "unit": UNIT,
+           "lanes": info["lanes"], "E_x": E, "roofline": rl}
+    golden = os.path.join(ROOT, "tests", "golden", "c2_fp32_n96_N64.json")
+    if os.path.exists(golden):
+        with open(golden) as fh:
+            rec["E_x_abs_err_vs_oracle_Ha"] = abs(E - json.load(fh)["E_x"])
+    return rec
+
+
+def fp32_vs_fp64_record(torch, dev, exx, synth, stream, ag):
+    """The metric's comparison per E_x + gradient (torch.autograd forward +
+    backward) on the 128-orbital 128^3 workload: FP32 against the plain FP64
+    GPU path, both against the stored FP64 oracle value of E_x."""
+    import numpy as np
+    name = "c3_grad_n128_N128"
+    r, psi64 = synth.workload(name, dtype=np.float64, device=dev)
+    occ = np.full(r.norb, r.occupation)
+    P = r.norb * (r.norb + 1) // 2
+
+    def step(plan, x):
+        def f():
+            x.grad = None
+            E = ag.exx_energy(x, plan)
+            E.backward()
+            return E
+        return f
+
+    p32 = exx.ExxPlan(r.n, r.h, r.alpha, occ, precision="fp32")
+    x32 = psi64.float().requires_grad_(True)
+    f32 = step(p32, x32)
+    f32()
+    ms32 = cuda_time(torch, stream, f32, 3)
+    E32 = float(f32().item())
+    g32 = x32.grad.detach().double()
+    p32.close()
+    del x32
+    p64 = exx.ExxPlan(r.n, r.h, r.alpha, occ, precision="fp64")
+    x64 = psi64.clone().requires_grad_(True)
+    f64 = step(p64, x64)
+    f64()
+    ms64 = cuda_time(torch, stream, f64, 1)
+    E64 = float(f64().item())
+    g64 = x64.grad.detach()
+    p64.close()
+    rel = float(torch.linalg.vector_norm(g32 - g64).item() / torch.linalg.vector_norm(g64).item())
+    rec = {"workload": f"{name}: 128 orbitals on 128^3 (256^3 padded), h = 0.37 -- the largest "
+                       "workload whose FP64 step fits the bench run (FP64 at 160^3 is not built)",
+           "pairs": P, "what": "ms per E_x + gradient: ExxEnergy forward + backward (torch.autograd)",
+           "fp32_ms_per_step": ms32, "fp64_plain_ms_per_step": ms64,
+           "fp32_speedup_vs_fp64_plain": ms64 / ms32,
+           "fp32_value": P / (ms32 * 1e-3), "fp64_value": P / (ms64 * 1e-3), "unit": UNIT,
+           "E_x_fp32": E32, "E_x_fp64": E64, "E_x_abs_diff_fp32_vs_fp64_Ha": abs(E32 - E64),
+           "gradient_rel_l2_fp32_vs_fp64": rel}
+    golden = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    if os.path.exists(golden):
+        with open(golden) as fh:
+            Eo = json.load(fh)["E_x"]
+        rec["E_x_fp32_abs_err_vs_oracle_Ha"] = abs(E32 - Eo)
+        rec["E_x_fp64_abs_err_vs_oracle_Ha"] = abs(E64 - Eo)
+    del psi64, x64
+    torch.cuda.empty_cache()
+    return rec
+
+
+def batched_record(torch, dev, exx, synth, ag, recipes, label, fp64=True):
+    """A batch of uneven molecules: FP32 batched (one CUDA-graph launch) apply
+    and autograd per step, against one FP32 plan per molecule and the plain
+    FP64 path (one FP64 plan per molecule, autograd)."""
+    import numpy as np
     mols, pt = [], []
     for r in recipes:
         mols.append({"n": r.n, "h": r.h, "alpha": r.alpha, "occupations": np.full(r.norb, r.occupation)})
-        pt.append(torch.from_numpy(synth.make_orbitals(r, dtype=np.float32)).to(dev))
+        pt.append(synth.make_orbitals(r, dtype=np.float64, device=dev))
+    p32 = [p.float() for p in pt]
     pairs = sum(r.norb * (r.norb + 1) // 2 for r in recipes)
     b = exx.ExxBatch(mols)
-    vx = [torch.empty_like(p) for p in pt]
-    b.set_buffers(pt, vx)
+    vx = [torch.empty_like(p) for p in p32]
+    b.set_buffers(p32, vx)
     b.graph(True)
     s = torch.cuda.Stream()
     E = torch.zeros(len(mols), dtype=torch.float64, device=dev)
     with torch.cuda.stream(s):
         for _ in range(2):
-            b.apply(E, stream=s)
-        s.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(s)
-        for _ in range(3):
-            b.apply(E, stream=s)
-        t1.record(s)
-    s.synchronize()
-    ms = t0.elapsed_time(t1) / 3
+            b.gradient(E, stream=s)
+        ms = cuda_time(torch, s, lambda: b.gradient(E, stream=s), 3)
     info = b.info()
+    # batched autograd: ExxBatchEnergy forward + backward
+    xs = [p.clone().requires_grad_(True) for p in p32]
+
+    def ag_step():
+        for x in xs:
+            x.grad = None
+        ag.exx_batch_energy(b, xs).sum().backward()
+    with torch.cuda.stream(s):  # graph replay needs a created stream
+        ag_step()
+        ms_ag = cuda_time(torch, s, ag_step, 3)
     b.close()
+    cur = torch.cuda.current_stream()
+    # one FP32 plan per molecule
     plans = [exx.ExxPlan(m["n"], m["h"], m["alpha"], m["occupations"], precision="fp32") for m in mols]
-    outs = [torch.empty_like(p) for p in pt]
-    for pl, p, o in zip(plans, pt, outs):
-        pl.apply_async(p, o)
-    torch.cuda.synchronize()
-    q0 = torch.cuda.Event(enable_timing=True)
-    q1 = torch.cuda.Event(enable_timing=True)
-    q0.record(stream)
-    for _ in range(3):
-        for pl, p, o in zip(plans, pt, outs):
-            pl.apply_async(p, o)
-    q1.record(stream)
-    torch.cuda.synchronize()
-    ms_seq = q0.elapsed_time(q1) / 3
+    outs = [torch.empty_like(p) for p in p32]
+
+    def seq():
+        for pl, p, o in zip(plans, p32, outs):
+            pl.gradient_async(p, o)
+    seq()
+    ms_seq = cuda_time(torch, cur, seq, 3)
     for pl in plans:
         pl.close()
-    return {"workload": "16 molecules, N_m in [8,96], n_m in {48,64,80,96,112,128}, h=0.4, seed 3",
-            "pairs": pairs, "ms_per_step": ms, "value": pairs / (ms * 1e-3), "unit": UNIT,
-            "graph": True, "groups": info["groups"], "waves": info["waves"],
-            "launches_per_step": info["launches_apply"],
-            "sequential_plans_ms": ms_seq, "speedup_vs_sequential_plans": ms_seq / ms}
+    rec = {"workload": label, "pairs": pairs, "ms_per_step": ms, "value": pairs / (ms * 1e-3),
+           "unit": UNIT, "graph": True, "groups": info["groups"], "waves": info["waves"],
+           "launches_per_step": info["launches_apply"],
+           "autograd_ms_per_step": ms_ag,
+           "sequential_plans_ms": ms_seq, "speedup_vs_sequential_plans": ms_seq / ms}
+    if fp64:
+        plans = [exx.ExxPlan(m["n"], m["h"], m["alpha"], m["occupations"], precision="fp64") for m in mols]
+        xs64 = [p.clone().requires_grad_(True) for p in pt]
+
+        def ag64():
+            for pl, x in zip(plans, xs64):
+                x.grad = None
+                ag.exx_energy(x, pl).backward()
+        ag64()
+        ms64 = cuda_time(torch, cur, ag64, 1)
+        for pl in plans:
+            pl.close()
+        rec["fp64_plain_autograd_ms_per_step"] = ms64
+        rec["fp32_batched_autograd_speedup_vs_fp64_plain"] = ms64 / ms_ag
+        del xs64
+    del pt, p32, xs
+    torch.cuda.empty_cache()
+    return rec
 
 
+# ------------------------------------------------------------ reference arm
 def run_reference(a):
+    """The FP64 oracle on the host cores, each step a bounded sample of the
+    workload's pair solves (a few seeded pairs among 16 seeded orbitals)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    import numpy as np
     from paper_1712_07973_gb300 import synth
-    r, psi = synth.workload(WORKLOAD)
-    per_step = 32
-    for _ in range(a.warmup):
-        cpu_oracle_rate(psi, r, per_step, seed=1)
-    rates, tot_t = [], 0.0
-    for k in range(a.steps):
-        rate, dt = cpu_oracle_rate(psi, r, per_step, seed=100 + k)
-        rates.append(rate)
-        tot_t += dt
-    value = per_step * a.steps / tot_t
-    P = r.norb * (r.norb + 1) // 2
+    r = synth.WORKLOADS[a.workload]
+    if a.norb:
+        r.norb = a.norb
+    N, P = r.norb, r.norb * (r.norb + 1) // 2
+    rng = np.random.default_rng(2024)
+    pool = np.sort(rng.choice(N, size=min(16, N), replace=False))
+    orbs = dict(zip(pool.tolist(), synth.orbital_subset(r, pool)))
+    Gh = oracle_spectrum(r.n, r.h, a.bc)
+    per_step = 2 if r.n >= 128 else 8
+    pool_pairs = [(int(i), int(j)) for k, i in enumerate(pool) for j in pool[k:]]
+
+    def one_step(seed):
+        sel = np.random.default_rng(seed).choice(len(pool_pairs), size=per_step, replace=False)
+        dt, _ = oracle_pairs(lambda i: orbs[i], [pool_pairs[s] for s in sel], r, Gh)
+        return dt
+
+    for k in range(a.warmup):
+        one_step(1 + k)
+    times = [one_step(100 + k) for k in range(a.steps)]
+    tot = sum(times)
+    value = per_step * a.steps / tot
     cores = os.cpu_count()
-    sample = f"{per_step} seeded pair solves per step of the {P} of the 64-orbital 96^3 workload"
+    sample = (f"{per_step} seeded pair solves per step (among the pairs of 16 seeded orbitals) of "
+              f"the {P} of the workload; FP64 NumPy/SciPy, scipy.fft workers = all cores")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * P / value,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
+        "ms_per_step_is": f"measured: one step = {per_step} sampled pair solves",
+        "ms_per_full_workload_extrapolated": 1e3 * P / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "norb": r.norb, "n": r.n,
-                                        "pairs": P, "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+        "data": "synthetic", "config": {"workload": a.workload, "norb": N, "n": r.n, "pairs": P,
+                                        "pairs_per_step": per_step, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -309,24 +537,26 @@ def run_ours(a):
     import numpy as np
     import torch
     rank, world, local = dist_env()
-    dist = None
+    tdist = None
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1712_07973_gb300 import build, exx, synth
+    from paper_1712_07973_gb300 import autograd as ag, build, dist as xdist, exx, synth
     build.build()
-    big = a.workload != WORKLOAD
-    if big:  # large inputs: generated with the device's help, never copied to the host
-        r, psi = synth.workload(a.workload, dtype=np.float32, device=dev)
-        psi_np = None
-    else:
+    small = a.workload == "c2_fp32_n96_N64"
+    if small:
         r, psi_np = synth.workload(a.workload)
         if a.norb:
             psi_np = psi_np[: a.norb].copy()
             r.norb = a.norb
         psi = torch.from_numpy(psi_np).to(dev, torch.float32)
+    else:  # large inputs: generated with the device's help, never copied to the host
+        r, psi = synth.workload(a.workload, dtype=np.float32, device=dev)
+        if a.norb:
+            psi = psi[: a.norb].contiguous()
+            r.norb = a.norb
     N, n = r.norb, r.n
     P = N * (N + 1) // 2
     occ = np.full(N, r.occupation)
@@ -338,12 +568,28 @@ def run_ours(a):
     E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
+    if tdist:
+        def step():
+            xdist.sharded_apply(plan, psi, out=out, gradient=True, sync=False)
+        parallelism = f"pair-tile sharding over {world} GPUs + NCCL all-reduce of E_x and the gradient"
+    else:
+        def step():
+            plan.gradient_async(psi, out, E_dev)
+        parallelism = "one GPU"
+
     for _ in range(a.warmup):
-        plan.apply_async(psi, out, E_dev)
+        step()
     torch.cuda.synchronize()
+    # one lane (plans whose slab kernels run as two-CTA clusters): every kernel
+    # alone on the stream, so the per-launch events of the roofline are taken
+    # in the headline region itself
+    inline_prof = info["lanes"] == 1 and not tdist
+    if inline_prof:
+        plan.profile(True)
+        plan.profile_read(reset=True)
     sampler = ClockSampler(local) if rank == 0 else None
-    if dist:
-        dist.barrier()
+    if tdist:
+        tdist.barrier()
     if sampler:
         sampler.start()
         time.sleep(0.3)
@@ -352,176 +598,140 @@ def run_ours(a):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(a.steps):
-        plan.apply_async(psi, out, E_dev)
+        step()
     t1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    if tdist:
+        tdist.barrier()
     clocks = sampler.stop() if sampler else None
     ms = t0.elapsed_time(t1)
-    if dist:
+    if tdist:
         tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
         ms = float(tt.item())
-    E = float(E_dev.item())
-    value = world * P * a.steps / (ms * 1e-3)
+    if tdist:
+        E = float(xdist.sharded_apply(plan, psi, out=out, gradient=True)[0])
+    else:
+        E = float(E_dev.item())
+    value = P * a.steps / (ms * 1e-3)
     ms_step = ms / a.steps
 
-    # roofline of the dominant kernel: a second timed region of the same steps
-    # with one pipeline lane (every kernel alone on the stream, as the two-lane
-    # headline region overlaps consecutive tiles) and CUDA events recorded by
-    # the library around every launch
-    plan.set_lanes(1)
-    plan.apply_async(psi, out, E_dev)
-    torch.cuda.synchronize()
-    plan.profile(True)
-    plan.profile_read(reset=True)
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for _ in range(a.steps):
-        plan.apply_async(psi, out, E_dev)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    ms_serial = s0.elapsed_time(s1) / a.steps
-    prof = plan.profile_read(reset=True)
-    plan.profile(False)
-    plan.set_lanes(info["lanes"])
-    alg = algorithmic_bytes(n, N, info["tile"], bc=a.bc)
-    dom = max(alg, key=lambda k: prof[k][0])
-    kms, kcnt = prof[dom]
-    per_launch_bytes = alg[dom] / (kcnt / a.steps)
-    achieved = per_launch_bytes / (kms / kcnt * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    shares = {k: round(v[0] / max(1e-9, sum(x[0] for x in prof.values())), 4) for k, v in prof.items()}
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": committed_traffic(dom), "algorithmic_bytes_per_launch": int(per_launch_bytes),
-                "avg_launch_ms": kms / kcnt, "kernel_shares": shares,
-                "timed_region": f"{a.steps} further steps, one pipeline lane, events around every launch",
-                "serialised_ms_per_step": ms_serial}
-
-    # whole pipeline: algorithmic bytes of all kernels of a step over the step time
-    step_bytes = sum(alg.values())
-    pipeline = {"algorithmic_bytes_per_step": int(step_bytes),
-                "bytes_per_pair": int(step_bytes / P),
-                "achieved": round(step_bytes / (ms_step * 1e-3) / 1e9, 1), "unit": "GB/s",
-                "frac": round(step_bytes / (ms_step * 1e-3) / 1e9 / peak, 4)}
-    roofline["pipeline"] = pipeline
-
+    alg = algorithmic_bytes(n, N, info["tile"], bc=a.bc)
+    if inline_prof:
+        prof = plan.profile_read(reset=True)
+        plan.profile(False)
+        region = f"the {a.steps} timed steps (one pipeline lane), events around every launch"
+        ms_serial = ms_step
+    elif not tdist:
+        # two lanes overlap consecutive tiles: a second region of the same
+        # steps with one lane times every kernel alone
+        plan.set_lanes(1)
+        step()
+        plan.profile(True)
+        plan.profile_read(reset=True)
+        ms_serial = cuda_time(torch, stream, step, a.steps)
+        prof = plan.profile_read(reset=True)
+        plan.profile(False)
+        plan.set_lanes(info["lanes"])
+        region = f"{a.steps} further steps, one pipeline lane, events around every launch"
+    else:
+        prof = None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if tdist else "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
             "config": {"workload": a.workload, "bc": a.bc, "norb": N, "n": n,
                        "fft_grid": [2 * hh for hh in half_lines(n, a.bc)], "h": r.h,
                        "pairs": P, "tile": info["tile"], "lanes": info["lanes"],
-                       "precision": "fp32 ffts, fp64 reductions",
-                       "l2": "inputs larger than L2 (psi 226 MB; pair-tile spectra 0.2-0.9 GB)",
-                       "parallelism": f"replicas x{world}"},
-            "E_x": E, "clocks": clocks, "roofline": roofline,
+                       "step": "E_x + gradient (exx_gradient: all pair solves, products, FP64 "
+                               "accumulation and energy)",
+                       "precision": "fp32 ffts and products, fp64 kernel, energies and accumulation",
+                       "l2": f"inputs larger than L2 (psi {N * n ** 3 * 4 / 1e9:.2f} GB; pair-tile "
+                             "spectra up to 4.2 GB): no flush needed",
+                       "parallelism": parallelism},
+            "E_x": E, "clocks": clocks,
             "gpu_launches": info["launches_apply"] * a.steps}
-    if per:
-        line["roofline"]["traffic"] = None  # the committed capture is of the free-BC kernels
+    if prof is not None:
+        rl = roofline_of(prof, alg, a.steps, peak, peak_kind, a.workload, region)
+        rl["serialised_ms_per_step"] = ms_serial
+        step_bytes = sum(alg.values())
+        rl["pipeline"] = {"algorithmic_bytes_per_step": int(step_bytes),
+                          "bytes_per_pair": int(step_bytes / P),
+                          "achieved": round(step_bytes / (ms_step * 1e-3) / 1e9, 1), "unit": "GB/s",
+                          "frac": round(step_bytes / (ms_step * 1e-3) / 1e9 / peak, 4)}
+        if per or a.norb:
+            rl["traffic"] = None  # the committed captures are of the free-BC workloads
+        line["roofline"] = rl
 
-    golden = os.path.join(ROOT, "tests", "golden", f"{a.workload}.json")
-    if a.norb or per:
-        golden = ""
-    if os.path.exists(golden):
-        with open(golden) as fh:
-            line["E_x_abs_err_vs_oracle_Ha"] = abs(E - json.load(fh)["E_x"])
+    # oracle sample: per-pair errors of the FP32 path and the CPU baseline
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and not a.norb and not per:
+        Eij = plan.pair_energies()
+        sp = sample_pairs(N, a.cpu_sample, seed=77)
+        Gh = oracle_spectrum(n, r.h, a.bc)
 
-    # e2e through the host-buffer entry point (pinned memory), every step copies
-    # psi in and Vx psi + E_x out
-    psi_h = (psi.cpu() if big else torch.from_numpy(psi_np.astype(np.float32))).pin_memory()
-    vx_h = torch.empty(psi_h.shape, dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, min(a.steps, 10))
-    plan.apply_host(psi_h, vx_h)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.apply_host(psi_h, vx_h)
-    w1 = time.perf_counter()
-    e2e_s = w1 - w0
-    if dist:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    nbytes = N * n ** 3 * 4
-    line["e2e"] = {"value": world * P * e2e_steps / e2e_s, "unit": UNIT,
-                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8,
-                   "api": "exx_apply_host"}
-
-    # autograd path: forward + hand-written backward through ExxEnergy (the
-    # backward is the exchange action computed in the same pair solves)
-    from paper_1712_07973_gb300 import autograd as ag
-    pg = psi.clone().requires_grad_(True)
-    for _ in range(2):
-        pg.grad = None
-        ag.exx_energy(pg, plan).backward()
-    torch.cuda.synchronize()
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    ag_steps = max(3, min(a.steps, 10))
-    a0.record(stream)
-    for _ in range(ag_steps):
-        pg.grad = None
-        ag.exx_energy(pg, plan).backward()
-    a1.record(stream)
-    torch.cuda.synchronize()
-    line["autograd"] = {"ms_per_step": a0.elapsed_time(a1) / ag_steps,
-                        "what": "E_x forward + gradient backward via torch.autograd"}
-    del pg
-
-    # FP64 plain GPU path on the same workload (the comparison the metric names)
-    if not a.no_fp64 and (not big or n <= 128):
-        p64 = exx.ExxPlan(n, r.h, r.alpha, occ, precision="fp64", kernel=kern)
-        if big:  # same seeded orbitals, generated in FP64 on the device
-            psi64 = synth.workload(a.workload, dtype=np.float64, device=dev)[1].to(torch.float64)
-        else:
-            psi64 = torch.from_numpy(psi_np).to(dev)
-        out64 = torch.empty(psi64.shape, dtype=torch.float64, device=dev)
-        p64.apply_async(psi64, out64, E_dev)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(2):
-            p64.apply_async(psi64, out64, E_dev)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1) / 2
-        E64 = float(E_dev.item())
-        line["fp64_plain"] = {"ms_per_step": ms64, "value": P / (ms64 * 1e-3), "unit": UNIT,
-                              "E_x": E64, "fp32_speedup": ms64 / ms_step,
-                              "autograd_fp32_speedup": ms64 / line["autograd"]["ms_per_step"],
-                              "E_x_abs_diff_fp32_vs_fp64_Ha": abs(E - E64)}
-        if os.path.exists(golden):
-            with open(golden) as fh:
-                line["fp64_plain"]["E_x_abs_err_vs_oracle_Ha"] = abs(E64 - json.load(fh)["E_x"])
-        p64.close()
-        del psi64, out64
-
-    if a.batched and not big:
-        line["batched"] = batched_line(torch, dev, exx, synth, stream)
-
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        sample = a.cpu_sample if not big else max(4, a.cpu_sample // 16)
-        if big:
-            psi_np = psi.double().cpu().numpy()
-        a.cpu_sample = sample
-        rate, dt = cpu_oracle_rate(psi_np, r, a.cpu_sample, bc=a.bc)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(),
-                                "kind": "oracle", "seconds": dt,
-                                "sample": f"{a.cpu_sample} seeded pair solves (of {P}) of the same "
+        def orb(i):
+            return psi[i].double().cpu().numpy()
+        dt, Eo = oracle_pairs(orb, [(i, j) for i, j, _ in sp], r, Gh)
+        errs = [abs(Eij[g] - Eo[(i, j)]) for i, j, g in sp]
+        w = [(1.0 if i == j else 2.0) * occ[i] * occ[j] * 0.5 * r.alpha for i, j, _ in sp]
+        est = (P / len(sp)) * sum(wk * (Eij[g] - Eo[(i, j)]) for wk, (i, j, g) in zip(w, sp))
+        line["pair_sample_vs_oracle"] = {
+            "pairs": len(sp), "max_abs_err_E_ij_Ha": max(errs),
+            "mean_abs_err_E_ij_Ha": sum(errs) / len(errs),
+            "E_x_error_estimate_Ha": abs(est),
+            "E_x_error_estimate_is": "sampled pairs' weighted errors scaled to all pairs (estimate)",
+            "inputs": "the FP32 orbitals of the GPU run, in FP64"}
+        line["cpu_baseline"] = {"value": len(sp) / dt, "unit": UNIT, "cores": os.cpu_count(),
+                                "cpu_model": cpu_model(), "kind": "oracle", "seconds": dt,
+                                "sample": f"{len(sp)} seeded pair solves (of {P}) of the same "
                                           "workload, FP64 NumPy/SciPy, scipy.fft workers = all cores"}
+        # out holds the gradient 2 f_k h^3 (Vx psi)_k, so E_x = 1/2 sum_k f_k h^3
+        # <psi_k, (Vx psi)_k> = 1/4 sum_k <psi_k, grad_k> (energy by Parseval in
+        # the z kernel, gradient in real space after every inverse transform)
+        cons = 0.25 * float((psi.double() * out.double()).sum().item())
+        line["E_x_vs_gradient_identity_rel"] = abs(cons - E) / abs(E)
+
+    # e2e through the host-buffer entry point (pinned memory): every step copies
+    # psi in and the gradient + E_x out
+    if not a.no_e2e and world == 1:
+        psi_h = psi.cpu().pin_memory()
+        g_h = torch.empty(psi_h.shape, dtype=torch.float32).pin_memory()
+        e2e_steps = 1 if not small else max(3, min(a.steps, 10))
+        plan.gradient_host(psi_h, g_h)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.gradient_host(psi_h, g_h)
+        e2e_s = time.perf_counter() - w0
+        nbytes = N * n ** 3 * 4
+        line["e2e"] = {"value": P * e2e_steps / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8,
+                       "api": "exx_gradient_host", "steps": e2e_steps}
+        del psi_h, g_h
     plan.close()
+    del out
+    torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not a.norb and not per:
+        if not a.no_fp64:
+            line["fp32_vs_fp64"] = fp32_vs_fp64_record(torch, dev, exx, synth, stream, ag)
+        if not a.no_c2 and not small:
+            line["c2"] = c2_record(torch, dev, exx, synth, stream, 10)
+        if a.batched:
+            line["batched"] = batched_record(
+                torch, dev, exx, synth, ag, synth.batched_workload(),
+                "16 molecules, N_m in [8,96], n_m in {48,64,80,96,112,128}, h=0.4, seed 3",
+                fp64=not a.no_fp64)
+            line["batched_small"] = batched_record(
+                torch, dev, exx, synth, ag, synth.small_batched_workload(),
+                "64 small molecules, N_m in [8,24], n_m in {32,40,48}, h=0.4, seed 5",
+                fp64=not a.no_fp64)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    if tdist:
+        tdist.barrier()
+        tdist.destroy_process_group()
     return 0
 
 

@@ -165,6 +165,25 @@ exx_status_t exx_apply_async(exx_plan_t plan, const void* psi, void* vxpsi, doub
                              void* cuda_stream);
 
 /*
+ * exx_gradient -- E_x and its gradient with respect to the orbitals,
+ *   grad_k = dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k   (Sec. 2, Eq. daction: the
+ *   Fock operator is the derivative of E_X with respect to the density
+ *   matrix; for real orbitals and the symmetric kernel the factor 2 f_k h^3
+ *   follows from rho_ij = psi_i psi_j and the h^3 quadrature),
+ * from the same pair solves as exx_apply: the per-orbital factor is folded
+ * into the FP64 accumulation, so no separate scaling pass is needed.
+ *   psi    device, as for exx_energy.
+ *   grad   device, same shape and dtype as exx_apply's vxpsi; overwritten.
+ *   E_out  host, may be NULL; if non-NULL the call synchronises the stream.
+ */
+exx_status_t exx_gradient(exx_plan_t plan, const void* psi, void* grad, double* E_out,
+                          void* cuda_stream);
+/* exx_gradient_async -- as exx_gradient with E_x written to device memory
+ * (E_dev: device, one double, may be NULL); never synchronises. */
+exx_status_t exx_gradient_async(exx_plan_t plan, const void* psi, void* grad, double* E_dev,
+                                void* cuda_stream);
+
+/*
  * exx_energy_async -- as exx_energy with E_x written to device memory; no sync.
  */
 exx_status_t exx_energy_async(exx_plan_t plan, const void* psi, double* E_dev,
@@ -203,6 +222,11 @@ exx_status_t exx_plan_info(exx_plan_t plan, int* tile, int* ntiles, size_t* work
  */
 exx_status_t exx_apply_host(exx_plan_t plan, const void* psi_host, void* vxpsi_host, double* E_out,
                             void* cuda_stream);
+/* exx_gradient_host -- exx_apply_host returning the gradient 2 f_k h^3
+ * (Vx psi)_k in grad_host (see exx_gradient); same buffers, overlap and
+ * synchronisation. */
+exx_status_t exx_gradient_host(exx_plan_t plan, const void* psi_host, void* grad_host,
+                               double* E_out, void* cuda_stream);
 
 /*
  * exx_plan_set_lanes -- number of pipeline lanes (1 to 3) of later calls.
@@ -254,7 +278,9 @@ exx_status_t exx_profile_read(exx_plan_t plan, double* ms, long long* launches, 
  * device addresses (cudaGetSymbolAddress), and any call whose (n, h, kernel)
  * differs from the previous one on that device builds the kernel spectrum on
  * the host, copies it in and synchronises the stream: make such calls before
- * any stream capture.  All calls on a device share the arrays, which keep the
+ * any stream capture.  That reload holds a per-device lock until the caller's
+ * stream has drained, so calls on the same device from other host threads
+ * wait meanwhile.  All calls on a device share the arrays, which keep the
  * last call's contents; calls that overlap on the GPU race and must be
  * serialised by the caller (one stream, or events).
  */
@@ -307,6 +333,11 @@ exx_status_t exx_batch_set_buffers(exx_batch_t batch, const float* const* psi,
  */
 exx_status_t exx_batch_apply(exx_batch_t batch, double* E_dev, void* cuda_stream);
 exx_status_t exx_batch_energy(exx_batch_t batch, double* E_dev, void* cuda_stream);
+/*
+ * exx_batch_gradient -- as exx_batch_apply, but the bound outputs receive the
+ * gradient 2 f_k h^3 (Vx psi)_k of each molecule's E_x (see exx_gradient).
+ */
+exx_status_t exx_batch_gradient(exx_batch_t batch, double* E_dev, void* cuda_stream);
 
 /*
  * exx_batch_graph -- enable (1) or disable (0) CUDA-graph execution: the next

@@ -367,24 +367,24 @@ int default_tile(int N, int requested) {
 // k_accum launch: vector width 2 when aligned, full-tile specialisations
 template <typename R, int VEC>
 void launch_accum_v(int mode, const R* psi, const R* V, double* acc, const double* occ,
-                    const Tile& t, double c, long long n3, cudaStream_t st) {
+                    const Tile& t, double c, double gs, long long n3, cudaStream_t st) {
   const int threads = 256;
   const unsigned blocks = (unsigned)((n3 / VEC + threads - 1) / threads);
   if (mode == 1)
     k_accum<R, 8, VEC, 1><<<blocks, threads, 0, st>>>(psi, V, acc, occ, t.i0, t.ti, t.j0, t.tj,
-                                                       t.diag, c, n3);
+                                                       t.diag, c, gs, n3);
   else if (mode == 2)
     k_accum<R, 8, VEC, 2><<<blocks, threads, 0, st>>>(psi, V, acc, occ, t.i0, t.ti, t.j0, t.tj,
-                                                       t.diag, c, n3);
+                                                       t.diag, c, gs, n3);
   else
     k_accum<R, 8, VEC, 0><<<blocks, threads, 0, st>>>(psi, V, acc, occ, t.i0, t.ti, t.j0, t.tj,
-                                                       t.diag, c, n3);
+                                                       t.diag, c, gs, n3);
 }
 template <typename R>
 void launch_accum(bool v2, int mode, const R* psi, const R* V, double* acc, const double* occ,
-                  const Tile& t, double c, long long n3, cudaStream_t st) {
-  if (v2) launch_accum_v<R, 2>(mode, psi, V, acc, occ, t, c, n3, st);
-  else launch_accum_v<R, 1>(mode, psi, V, acc, occ, t, c, n3, st);
+                  const Tile& t, double c, double gs, long long n3, cudaStream_t st) {
+  if (v2) launch_accum_v<R, 2>(mode, psi, V, acc, occ, t, c, gs, n3, st);
+  else launch_accum_v<R, 1>(mode, psi, V, acc, occ, t, c, gs, n3, st);
 }
 
 extern "C" {
@@ -645,8 +645,11 @@ struct HostOverlap {
   const std::vector<cudaEvent_t>* out;
 };
 
+// apply: also the inverse transforms and the accumulation into vxpsi, which
+// receives (Vx psi)_k (grad = false) or dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k
+// (grad = true).
 static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_dev, bool apply,
-                        cudaStream_t st, const HostOverlap* ov = nullptr) {
+                        cudaStream_t st, const HostOverlap* ov = nullptr, bool grad = false) {
   const int n = p->n, N = p->N;
   const long long n3 = (long long)n * n * n;
   const double h3 = p->h * p->h * p->h;
@@ -657,6 +660,7 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
     EXX_CUDA(p, cudaMemsetAsync(acc, 0, (size_t)N * n3 * sizeof(double), st));
   }
   const double c = -p->alpha;
+  const double gs = grad ? 2.0 * h3 : 0.0;
   if (p->sharded)  // pair energies of other ranks' tiles must read as zero
     EXX_CUDA(p, cudaMemsetAsync(p->Epair, 0, (size_t)p->P * sizeof(double), st));
   // Lanes: consecutive tiles go round-robin over the lanes' streams, each with
@@ -729,10 +733,10 @@ static exx_status_t run(exx_plan_t p, const void* psi, void* vxpsi, double* E_de
       const int mode = (t.ti == 8 && t.tj == 8) ? (t.diag ? 2 : 1) : 0;
       if (p->prec == EXX_FP64)
         launch_accum<double>(v2, mode, static_cast<const double*>(psi),
-                             static_cast<const double*>(Vt), acc, p->d_occ, t, c, n3, st);
+                             static_cast<const double*>(Vt), acc, p->d_occ, t, c, gs, n3, st);
       else
         launch_accum<float>(v2, mode, static_cast<const float*>(psi),
-                            static_cast<const float*>(Vt), acc, p->d_occ, t, c, n3, st);
+                            static_cast<const float*>(Vt), acc, p->d_occ, t, c, gs, n3, st);
       if (nl > 1) EXX_CUDA(p, cudaEventRecord(p->ev_free[l], st));
     }
     const bool row_end = ti + 1 == p->tiles.size() || p->tiles[ti + 1].i0 != t.i0;
@@ -774,6 +778,12 @@ exx_status_t exx_apply_async(exx_plan_t p, const void* psi, void* vxpsi, double*
   return run(p, psi, vxpsi, E_dev, true, static_cast<cudaStream_t>(cuda_stream));
 }
 
+exx_status_t exx_gradient_async(exx_plan_t p, const void* psi, void* grad, double* E_dev,
+                                void* cuda_stream) {
+  if (p == nullptr || psi == nullptr || grad == nullptr) return EXX_ERR_INVALID_ARG;
+  return run(p, psi, grad, E_dev, true, static_cast<cudaStream_t>(cuda_stream), nullptr, true);
+}
+
 exx_status_t exx_energy_async(exx_plan_t p, const void* psi, double* E_dev, void* cuda_stream) {
   if (p == nullptr || psi == nullptr) return EXX_ERR_INVALID_ARG;
   return run(p, psi, nullptr, E_dev, false, static_cast<cudaStream_t>(cuda_stream));
@@ -800,6 +810,16 @@ exx_status_t exx_apply(exx_plan_t p, const void* psi, void* vxpsi, double* E_out
   return check_wait_flag(p, st);
 }
 
+exx_status_t exx_gradient(exx_plan_t p, const void* psi, void* grad, double* E_out,
+                          void* cuda_stream) {
+  if (p == nullptr || psi == nullptr || grad == nullptr) return EXX_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  exx_status_t s = run(p, psi, grad, nullptr, true, st, nullptr, true);
+  if (s != EXX_OK || E_out == nullptr) return s;
+  EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  return check_wait_flag(p, st);
+}
+
 exx_status_t exx_energy(exx_plan_t p, const void* psi, double* E_out, void* cuda_stream) {
   if (p == nullptr || psi == nullptr || E_out == nullptr) return EXX_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -809,8 +829,9 @@ exx_status_t exx_energy(exx_plan_t p, const void* psi, double* E_out, void* cuda
   return check_wait_flag(p, st);
 }
 
-exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host, double* E_out,
-                            void* cuda_stream) {
+// exx_apply_host / exx_gradient_host: orbitals and results in host memory
+static exx_status_t run_host(exx_plan_t p, const void* psi_host, void* vxpsi_host, double* E_out,
+                             void* cuda_stream, bool grad) {
   if (p == nullptr || psi_host == nullptr || vxpsi_host == nullptr) return EXX_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const size_t cnt = (size_t)p->N * p->n * p->n * p->n;
@@ -826,7 +847,7 @@ exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host
   }
   if (p->sharded) {  // partial results: one copy each way around the pipeline
     EXX_CUDA(p, cudaMemcpyAsync(p->h_psi, psi_host, cnt * ps, cudaMemcpyHostToDevice, st));
-    exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st);
+    exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st, nullptr, grad);
     if (s != EXX_OK) return s;
     EXX_CUDA(p, cudaMemcpyAsync(vxpsi_host, p->h_vx, cnt * vs, cudaMemcpyDeviceToHost, st));
     if (E_out) EXX_CUDA(p, cudaMemcpyAsync(E_out, p->E_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -859,7 +880,7 @@ exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host
     EXX_CUDA(p, cudaEventRecord(p->ev_in[b], p->cst));
   }
   HostOverlap ov{&p->ev_in, &p->ev_out};
-  exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st, &ov);
+  exx_status_t s = run(p, p->h_psi, p->h_vx, nullptr, true, st, &ov, grad);
   if (s != EXX_OK) {
     cudaStreamSynchronize(p->cst);
     return s;
@@ -875,6 +896,16 @@ exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host
   EXX_CUDA(p, cudaEventRecord(p->ev_join, p->cst));
   EXX_CUDA(p, cudaStreamWaitEvent(st, p->ev_join, 0));
   return check_wait_flag(p, st);
+}
+
+exx_status_t exx_apply_host(exx_plan_t p, const void* psi_host, void* vxpsi_host, double* E_out,
+                            void* cuda_stream) {
+  return run_host(p, psi_host, vxpsi_host, E_out, cuda_stream, false);
+}
+
+exx_status_t exx_gradient_host(exx_plan_t p, const void* psi_host, void* grad_host, double* E_out,
+                               void* cuda_stream) {
+  return run_host(p, psi_host, grad_host, E_out, cuda_stream, true);
 }
 
 exx_status_t exx_plan_set_lanes(exx_plan_t p, int lanes) {

@@ -146,9 +146,9 @@ struct exx_batch_s {
   cudaEvent_t ev_fork = nullptr, ev_done[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // graph capture
   bool graph_on = false;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [apply, energy]
-  double* gE[2] = {nullptr, nullptr};
-  cudaStream_t gstream[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // [apply, energy, gradient]
+  double* gE[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t gstream[3] = {nullptr, nullptr, nullptr};
   std::string err;
 };
 
@@ -164,7 +164,7 @@ void batch_free(exx_batch_t b) {
     if (g.Gs) cudaFree(g.Gs);
     if (g.tw) cudaFree(g.tw);
   }
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 3; ++k)
     if (b->gexec[k]) cudaGraphExecDestroy(b->gexec[k]);
   for (void* q : {static_cast<void*>(b->epart2), b->X_2, b->V_2})
     if (q) cudaFree(q);
@@ -187,7 +187,9 @@ template <typename T> bool balloc(exx_batch_t b, T** p, size_t bytes) {
   return true;
 }
 
-exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, cudaStream_t st) {
+// apply: Vx psi (grad = false) or the gradient 2 f_k h^3 (Vx psi)_k (grad =
+// true) into the bound outputs
+exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, bool grad, cudaStream_t st) {
   if (apply) {
     long long tot = 0;
     for (const Mol& m : b->mol) tot += (long long)m.N * m.n * m.n * m.n;
@@ -233,11 +235,11 @@ exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, cudaStream_t st) 
         if (v2)
           k_accum_batch<float, 8, 2><<<dim3((unsigned)blocks, w.ntile), threads, 0, st>>>(
               b->d_psi_tab, static_cast<const float*>(Vl[l]), b->d_vacc_tab, b->d_occ,
-              b->d_tiles + w.tile_off, n3);
+              b->d_tiles + w.tile_off, grad ? 1 : 0, n3);
         else
           k_accum_batch<float, 8, 1><<<dim3((unsigned)blocks, w.ntile), threads, 0, st>>>(
               b->d_psi_tab, static_cast<const float*>(Vl[l]), b->d_vacc_tab, b->d_occ,
-              b->d_tiles + w.tile_off, n3);
+              b->d_tiles + w.tile_off, grad ? 1 : 0, n3);
         if (nl > 1 && cudaEventRecord(b->ev_free[l], st) != cudaSuccess) return EXX_ERR_CUDA;
       }
     }
@@ -258,11 +260,11 @@ exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, cudaStream_t st) 
   return cudaGetLastError() == cudaSuccess ? EXX_OK : EXX_ERR_CUDA;
 }
 
-exx_status_t run_batch(exx_batch_t b, double* E_dev, bool apply, cudaStream_t st) {
+exx_status_t run_batch(exx_batch_t b, double* E_dev, bool apply, bool grad, cudaStream_t st) {
   if (!b->buffers_set) return EXX_ERR_INVALID_ARG;
   if (apply && !b->have_vx) return EXX_ERR_INVALID_ARG;
-  const int k = apply ? 0 : 1;
-  if (!b->graph_on) return enqueue(b, E_dev, apply, st);
+  const int k = apply ? (grad ? 2 : 0) : 1;
+  if (!b->graph_on) return enqueue(b, E_dev, apply, grad, st);
   if (st == nullptr) return EXX_ERR_INVALID_ARG;  // capture needs a created stream
   if (b->gexec[k] && (b->gE[k] != E_dev || b->gstream[k] != st)) {
     cudaGraphExecDestroy(b->gexec[k]);
@@ -273,7 +275,7 @@ exx_status_t run_batch(exx_batch_t b, double* E_dev, bool apply, cudaStream_t st
       cudaGetLastError();
       return EXX_ERR_CUDA;
     }
-    exx_status_t s = enqueue(b, E_dev, apply, st);
+    exx_status_t s = enqueue(b, E_dev, apply, grad, st);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (s != EXX_OK || e != cudaSuccess) {
@@ -376,6 +378,7 @@ exx_status_t exx_batch_create(exx_batch_t* out, int nmol, const exx_mol_desc* mo
           t.mol = g.mols[k];
           t.occ_off = m.occ_off;
           t.c = -m.alpha;
+          t.g2h3 = 2.0 * m.h * m.h * m.h;
           t.voff = 0;
           std::vector<int4> ps;
           for (int a = 0; a < t.ti; ++a)
@@ -546,7 +549,7 @@ exx_status_t exx_batch_set_buffers(exx_batch_t b, const float* const* psi, float
   bool v2 = true;
   for (int m = 0; m < b->nmol; ++m) v2 = v2 && ((uintptr_t)p[m] % 8 == 0);
   if (v2 != b->vec2 || have != b->have_vx) {  // the captured graphs embed these choices
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 3; ++k)
       if (b->gexec[k]) {
         cudaGraphExecDestroy(b->gexec[k]);
         b->gexec[k] = nullptr;
@@ -560,12 +563,17 @@ exx_status_t exx_batch_set_buffers(exx_batch_t b, const float* const* psi, float
 
 exx_status_t exx_batch_apply(exx_batch_t b, double* E_dev, void* cuda_stream) {
   if (b == nullptr || E_dev == nullptr) return EXX_ERR_INVALID_ARG;
-  return run_batch(b, E_dev, true, static_cast<cudaStream_t>(cuda_stream));
+  return run_batch(b, E_dev, true, false, static_cast<cudaStream_t>(cuda_stream));
+}
+
+exx_status_t exx_batch_gradient(exx_batch_t b, double* E_dev, void* cuda_stream) {
+  if (b == nullptr || E_dev == nullptr) return EXX_ERR_INVALID_ARG;
+  return run_batch(b, E_dev, true, true, static_cast<cudaStream_t>(cuda_stream));
 }
 
 exx_status_t exx_batch_energy(exx_batch_t b, double* E_dev, void* cuda_stream) {
   if (b == nullptr || E_dev == nullptr) return EXX_ERR_INVALID_ARG;
-  return run_batch(b, E_dev, false, static_cast<cudaStream_t>(cuda_stream));
+  return run_batch(b, E_dev, false, false, static_cast<cudaStream_t>(cuda_stream));
 }
 
 exx_status_t exx_batch_graph(exx_batch_t b, int enable) {

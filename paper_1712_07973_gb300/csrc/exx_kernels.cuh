@@ -759,12 +759,15 @@ __device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
 // compile-time constant, so that all loads of a J step can be issued at once
 // (with the register budget of two CTAs per SM: 4.9 -> 3.8 ms per exx_apply
 // at n = 96, 64 orbitals).
+// gs = 0: the exchange action, vx_k += c * sum; gs > 0: the gradient of E_x,
+// vx_k += c gs f_k * sum (gs = 2 h^3: dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k,
+// Eq. daction), the per-orbital factor folded into the FP64 accumulation.
 template <typename R, int TM, int VEC, int MODE>
 __device__ __forceinline__ void accum_tile(const R* __restrict__ psi, const R* __restrict__ V,
                                            double* __restrict__ vx,
                                            const double* __restrict__ occ, int i0, int ti_,
-                                           int j0, int tj_, int diag_, double c, long long n3,
-                                           long long r) {
+                                           int j0, int tj_, int diag_, double c, double gs,
+                                           long long n3, long long r) {
   const int ti = MODE ? TM : ti_, tj = MODE ? TM : tj_;
   const bool diag = MODE == 2 ? true : MODE == 1 ? false : diag_ != 0;
   R fi[TM];
@@ -807,22 +810,26 @@ __device__ __forceinline__ void accum_tile(const R* __restrict__ psi, const R* _
 #pragma unroll
       for (int e = 0; e < VEC; ++e) ai[b][e] += aj[e];
     } else {
-      vacc<R, VEC>(vx + (long long)(j0 + b) * n3 + r, c, aj);
+      const double cb = gs != 0.0 ? c * (gs * occ[j0 + b]) : c;
+      vacc<R, VEC>(vx + (long long)(j0 + b) * n3 + r, cb, aj);
     }
   }
 #pragma unroll
   for (int a = 0; a < TM; ++a)
-    if (a < ti) vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, c, ai[a]);
+    if (a < ti) {
+      const double ca = gs != 0.0 ? c * (gs * occ[i0 + a]) : c;
+      vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, ca, ai[a]);
+    }
 }
 
 template <typename R, int TM, int VEC, int MODE>
 __global__ void __launch_bounds__(256, (sizeof(R) == 4 && MODE == 0) ? 3 : 2)
 k_accum(const R* __restrict__ psi, const R* __restrict__ V, double* __restrict__ vx,
         const double* __restrict__ occ, int i0, int ti, int j0, int tj, int diag, double c,
-        long long n3) {
+        double gs, long long n3) {
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
   if (r >= n3) return;
-  accum_tile<R, TM, VEC, MODE>(psi, V, vx, occ, i0, ti, j0, tj, diag, c, n3, r);
+  accum_tile<R, TM, VEC, MODE>(psi, V, vx, occ, i0, ti, j0, tj, diag, c, gs, n3, r);
 }
 
 // Tile descriptor of a batched wave (tiles of different molecules, or of
@@ -833,15 +840,16 @@ struct TileDesc {
   int mol;    // molecule slot: psi_tab[mol], vx_tab[mol], occ + occ_off[mol]
   int occ_off;
   double c;   // -alpha of the molecule
+  double g2h3;  // 2 h^3 of the molecule (gradient calls)
 };
 
 // One tile per blockIdx.y; full tiles take the specialised bodies (the branch
-// is uniform over a block).
+// is uniform over a block).  grad != 0: gradient of E_x (see accum_tile).
 template <typename R, int TM, int VEC>
 __global__ void __launch_bounds__(256, 2)
 k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
               double* const* __restrict__ vx_tab, const double* __restrict__ occ,
-              const TileDesc* __restrict__ tiles, long long n3) {
+              const TileDesc* __restrict__ tiles, int grad, long long n3) {
   const TileDesc t = tiles[blockIdx.y];
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
   if (r >= n3) return;
@@ -849,13 +857,14 @@ k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
   double* __restrict__ vx = vx_tab[t.mol];
   const double* __restrict__ oc = occ + t.occ_off;
   const R* __restrict__ Vt = V + (long long)t.voff * n3;
+  const double gs = grad ? t.g2h3 : 0.0;
   if (t.ti == TM && t.tj == TM) {
     if (t.diag)
-      accum_tile<R, TM, VEC, 2>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 1, t.c, n3, r);
+      accum_tile<R, TM, VEC, 2>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 1, t.c, gs, n3, r);
     else
-      accum_tile<R, TM, VEC, 1>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 0, t.c, n3, r);
+      accum_tile<R, TM, VEC, 1>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 0, t.c, gs, n3, r);
   } else {
-    accum_tile<R, TM, VEC, 0>(psi, Vt, vx, oc, t.i0, t.ti, t.j0, t.tj, t.diag, t.c, n3, r);
+    accum_tile<R, TM, VEC, 0>(psi, Vt, vx, oc, t.i0, t.ti, t.j0, t.tj, t.diag, t.c, gs, n3, r);
   }
 }
 

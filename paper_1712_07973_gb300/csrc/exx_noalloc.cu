@@ -11,8 +11,9 @@
 // file-scope device arrays below, and never allocates device memory.
 //
 // The arrays are sized for grids up to EXX_NOALLOC_MAX_N points per axis
-// (about 18 MB in total); every GPU that loads the library keeps them until
-// the process exits.  In host code an array's name is only a host-side
+// (about 29 MB in total: 14.3 MB of spectrum and 14.3 MB of kernel table at
+// n = 96); every GPU that loads the library keeps them until the process
+// exits.  In host code an array's name is only a host-side
 // stand-in, so the device addresses are looked up once per device with
 // cudaGetSymbolAddress and passed to the kernels as plain pointers.
 #include <cuda_runtime.h>
@@ -49,13 +50,21 @@ static __device__ __align__(256) double g_noalloc_epart[kEpartElems];
 static __device__ __align__(256) int4 g_noalloc_pair[1];
 static __device__ int g_noalloc_err[2];  // [0] set by a device-side wait that ran out; [1] test hook
 
+// the stated footprint (about 29 MB) cannot drift from the array sizes
+constexpr size_t kNoallocBytes = kSpecElems * sizeof(float2) + kKernElems * sizeof(float) +
+                                 kTwElems * sizeof(float2) + kEpartElems * sizeof(double) +
+                                 sizeof(int4) + 2 * sizeof(int);
+static_assert(kNoallocBytes > 28u * 1000 * 1000 && kNoallocBytes < 29u * 1000 * 1000,
+              "static scratch of exx_pair_energy_noalloc: about 29 MB");
+
 namespace {
 
 constexpr int kMaxN = kNoallocMaxN;
 
 // Per-device addresses of the arrays and the (n, h, kernel) whose spectrum and
-// twiddles they currently hold.
+// twiddles they currently hold, guarded by the device's own mutex.
 struct DeviceScratch {
+  std::mutex mu;
   bool ready = false;
   float2* spec = nullptr;
   float* kern = nullptr;
@@ -69,7 +78,6 @@ struct DeviceScratch {
   int kind = -1;
 };
 constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
 DeviceScratch g_noalloc_dev[kMaxDevices];
 
 __global__ void k_noalloc_set_pair(int i, int j) { g_noalloc_pair[0] = make_int4(i, j, 0, 0); }
@@ -155,10 +163,16 @@ extern "C" exx_status_t exx_pair_energy_noalloc(int n, double h, int kernel, con
     cudaGetLastError();
     return EXX_ERR_CUDA;
   }
-  DeviceScratch* d = nullptr;
+  // Under the device's lock: set-up, and a copy of everything the launches
+  // below read, so that no field of the shared record is read after the lock
+  // is released (another thread may reload the tables for other (n, h, kernel)
+  // meanwhile; its GPU work is ordered with this call's only by the caller).
+  // A reload synchronises the caller's stream while holding the lock, so
+  // calls on the same device from other threads wait until that stream drains.
+  DeviceScratch local_copy;
   {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    d = &g_noalloc_dev[dev];
+    DeviceScratch* d = &g_noalloc_dev[dev];
+    std::lock_guard<std::mutex> lock(d->mu);
     if (!d->ready) {
       const exx_status_t s = lookup_addresses(*d);
       if (s != EXX_OK) return s;
@@ -167,15 +181,23 @@ extern "C" exx_status_t exx_pair_energy_noalloc(int n, double h, int kernel, con
       const exx_status_t s = load_tables(*d, ops, n, h, kernel, st);
       if (s != EXX_OK) return s;
     }
+    local_copy.spec = d->spec;
+    local_copy.kern = d->kern;
+    local_copy.tw = d->tw;
+    local_copy.epart = d->epart;
+    local_copy.pair = d->pair;
+    local_copy.err = d->err;
+    local_copy.gmap = d->gmap;
   }
+  const DeviceScratch& d = local_copy;
   // Every scratch element read below is first written by this call (the pair
   // slot, the n-sized part of the spectrum, the column-block partials), so
   // nothing needs clearing.
   const long long n3 = (long long)n * n * n;
   k_noalloc_set_pair<<<1, 1, 0, st>>>(i, j);
-  ops->fwd_xy(psi, nullptr, d->pair, 1, d->spec, d->tw, n3, st);
-  ops->zconv(d->spec, d->kern, d->tw, &d->gmap, d->epart, d->err, 1, true, st);
-  k_noalloc_pair_total<<<1, 32, 0, st>>>(d->epart, (n + 1) * ops->nyb, h * h * h, d->err, E_dev);
+  ops->fwd_xy(psi, nullptr, d.pair, 1, d.spec, d.tw, n3, st);
+  ops->zconv(d.spec, d.kern, d.tw, &d.gmap, d.epart, d.err, 1, true, st);
+  k_noalloc_pair_total<<<1, 32, 0, st>>>(d.epart, (n + 1) * ops->nyb, h * h * h, d.err, E_dev);
   if (cudaGetLastError() != cudaSuccess) return EXX_ERR_CUDA;
   return EXX_OK;
 }

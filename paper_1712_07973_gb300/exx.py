@@ -39,12 +39,18 @@ EXPORTS = {
                                        ctypes.c_void_p, ctypes.c_void_p]),
     "exx_energy_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "exx_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _c_double_p,
+                                    ctypes.c_void_p]),
+    "exx_gradient_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "exx_pair_energies": (ctypes.c_int, [ctypes.c_void_p, _c_double_p, ctypes.c_void_p]),
     "exx_plan_info": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, _c_size_p, _c_int_p,
                                      _c_int_p]),
     "exx_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "exx_apply_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _c_double_p,
                                       ctypes.c_void_p]),
+    "exx_gradient_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         _c_double_p, ctypes.c_void_p]),
     "exx_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "exx_plan_set_lanes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "exx_plan_get_lanes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
@@ -63,6 +69,7 @@ EXPORTS = {
                                              ctypes.c_void_p]),
     "exx_batch_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "exx_batch_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "exx_batch_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "exx_batch_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "exx_batch_pair_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_double_p,
                                                ctypes.c_void_p]),
@@ -250,6 +257,33 @@ class ExxPlan:
                                   _stream_ptr(stream)), "exx_apply", self.handle)
         return E.value, out
 
+    def _out(self, psi, out):
+        import torch
+        if out is None:
+            return torch.empty(psi.shape, dtype=self.vx_dtype, device=psi.device)
+        if out.dtype != self.vx_dtype or out.shape != psi.shape or not out.is_contiguous():
+            raise ExxError(1, "output", f"contiguous {self.vx_dtype} tensor of psi's shape required")
+        return out
+
+    def gradient(self, psi, out=None, stream=None):
+        """(E_x, dE_x/dpsi): the energy and its gradient 2 f_k h^3 (Vx psi)_k,
+        the per-orbital factor applied inside the library (exx_gradient)."""
+        p = self._psi(psi)
+        out = self._out(psi, out)
+        E = ctypes.c_double()
+        _check(self.lib.exx_gradient(self.handle, p, ctypes.c_void_p(out.data_ptr()), ctypes.byref(E),
+                                     _stream_ptr(stream)), "exx_gradient", self.handle)
+        return E.value, out
+
+    def gradient_async(self, psi, out, E_dev=None, stream=None):
+        """exx_gradient without synchronising (E_x into the device tensor E_dev)."""
+        p = self._psi(psi)
+        out = self._out(psi, out)
+        e = ctypes.c_void_p(E_dev.data_ptr()) if E_dev is not None else ctypes.c_void_p()
+        _check(self.lib.exx_gradient_async(self.handle, p, ctypes.c_void_p(out.data_ptr()), e,
+                                           _stream_ptr(stream)), "exx_gradient_async", self.handle)
+        return out
+
     def apply_async(self, psi, out, E_dev=None, stream=None):
         """exx_apply without synchronising: Vx psi into out and, if given, E_x
         into the one-element FP64 device tensor E_dev (graph-capturable)."""
@@ -280,6 +314,14 @@ class ExxPlan:
         _check(self.lib.exx_apply_host(self.handle, ctypes.c_void_p(_host_ptr(psi_host)),
                                        ctypes.c_void_p(_host_ptr(vx_host)), ctypes.byref(E),
                                        _stream_ptr(stream)), "exx_apply_host", self.handle)
+        return E.value
+
+    def gradient_host(self, psi_host, grad_host, stream=None):
+        """exx_gradient_host on (page-locked) host tensors/arrays; returns E_x."""
+        E = ctypes.c_double()
+        _check(self.lib.exx_gradient_host(self.handle, ctypes.c_void_p(_host_ptr(psi_host)),
+                                          ctypes.c_void_p(_host_ptr(grad_host)), ctypes.byref(E),
+                                          _stream_ptr(stream)), "exx_gradient_host", self.handle)
         return E.value
 
     KINDS = ("fwd_xy", "zconv", "pair_energy", "inv_yx", "accum", "exx_total", "to_float")
@@ -401,6 +443,16 @@ class ExxBatch:
             E_dev = torch.zeros(self.nmol, dtype=torch.float64, device="cuda")
         _check(self.lib.exx_batch_apply(self.handle, ctypes.c_void_p(E_dev.data_ptr()),
                                         _stream_ptr(stream)), "exx_batch_apply")
+        return E_dev
+
+    def gradient(self, E_dev=None, stream=None):
+        """E_x per molecule (FP64 device tensor) and the gradients
+        2 f_k h^3 (Vx psi)_k into the bound outputs, asynchronously."""
+        import torch
+        if E_dev is None:
+            E_dev = torch.zeros(self.nmol, dtype=torch.float64, device="cuda")
+        _check(self.lib.exx_batch_gradient(self.handle, ctypes.c_void_p(E_dev.data_ptr()),
+                                           _stream_ptr(stream)), "exx_batch_gradient")
         return E_dev
 
     def energy(self, E_dev=None, stream=None):

@@ -23,7 +23,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["OrbitalRecipe", "make_orbitals", "workload", "WORKLOADS", "batched_workload"]
+__all__ = ["OrbitalRecipe", "make_orbitals", "orbital_subset", "workload", "WORKLOADS",
+           "batched_workload", "small_batched_workload"]
 
 
 @dataclass
@@ -128,6 +129,62 @@ def _make_orbitals_torch(r: OrbitalRecipe, dtype, device):
     return psi.to(tdt).contiguous()
 
 
+def _terms(r: OrbitalRecipe):
+    """The separable terms of every orbital, with the same random draws as
+    make_orbitals: per-axis profiles Z, Y, X (coefficient folded into Z) of
+    shape (norb * G, n) and the orbital of each term."""
+    rng = np.random.default_rng(r.seed)
+    sites = _sites(rng, r)
+    x = np.arange(r.n, dtype=np.float64) * r.h
+    G = r.gauss_per_orb
+    Z, Y, X = [], [], []
+    for o in range(r.norb):
+        at = rng.integers(0, r.nsites, size=G)
+        sig = rng.uniform(r.sigma[0], r.sigma[1], size=G)
+        coef = rng.standard_normal(G)
+        typ = rng.integers(0, 4, size=G) if r.p_type else np.zeros(G, int)
+        R = sites[at]
+        s2 = 2.0 * sig ** 2
+        dz = x[None, :] - R[:, 2, None]                 # (G, n)
+        dy = x[None, :] - R[:, 1, None]
+        dx = x[None, :] - R[:, 0, None]
+        Z.append(np.exp(-dz * dz / s2[:, None]) * np.where(typ[:, None] == 3, dz, 1.0) * coef[:, None])
+        Y.append(np.exp(-dy * dy / s2[:, None]) * np.where(typ[:, None] == 2, dy, 1.0))
+        X.append(np.exp(-dx * dx / s2[:, None]) * np.where(typ[:, None] == 1, dx, 1.0))
+    owner = np.repeat(np.arange(r.norb), G)
+    return np.concatenate(Z), np.concatenate(Y), np.concatenate(X), owner
+
+
+def orbital_subset(r: OrbitalRecipe, idx, chunk=1024):
+    """Orbitals idx of the workload (the rows psi[idx] of make_orbitals, to
+    rounding) without forming the others: every orbital is a sum of separable
+    terms, so the overlap matrix S_ij = h^3 sum_m phi_i phi_j is a sum of
+    products of one-dimensional overlaps, and psi_k = sum_j (S^-1/2)_kj phi_j
+    is a weighted sum of the separable terms.  Memory O(norb^2 G^2 / blocks +
+    len(idx) n^3); used for large workloads on the host."""
+    Z, Y, X, owner = _terms(r)
+    N, G, n = r.norb, r.gauss_per_orb, r.n
+    S = np.zeros((N, N))
+    for b0 in range(0, N, max(1, chunk // G)):
+        b1 = min(N, b0 + max(1, chunk // G))
+        rows = slice(b0 * G, b1 * G)
+        W = (Z[rows] @ Z.T) * (Y[rows] @ Y.T) * (X[rows] @ X.T)   # term overlaps
+        S[b0:b1] = W.reshape(b1 - b0, G, N, G).sum(axis=(1, 3))
+    S *= r.h ** 3
+    S = 0.5 * (S + S.T)
+    w, U = np.linalg.eigh(S)
+    Sm12 = (U / np.sqrt(w)) @ U.T
+    idx = np.asarray(idx, dtype=np.int64)
+    A = Sm12[idx][:, owner]                                       # (K, terms)
+    out = np.zeros((len(idx), n, n * n))
+    for t0 in range(0, Z.shape[0], chunk):
+        t1 = min(Z.shape[0], t0 + chunk)
+        YX = (Y[t0:t1, :, None] * X[t0:t1, None, :]).reshape(t1 - t0, n * n)
+        for k in range(len(idx)):
+            out[k] += (Z[t0:t1] * A[k, t0:t1, None]).T @ YX
+    return out.reshape(len(idx), n, n, n)
+
+
 # Workloads: the five configurations the benchmarks and parity tests use.
 WORKLOADS = {
     # plain FP64: 4 orbitals, 32^3 grid (64^3 padded), 3 s-Gaussians each
@@ -163,3 +220,10 @@ def batched_workload(seed=3, nmol=16, grids=(48, 64, 80, 96, 112, 128), nrange=(
                                  seed=int(rng.integers(0, 2 ** 31 - 1)),
                                  gauss_per_orb=16, sigma=(0.7, 1.8), p_type=True))
     return out
+
+
+def small_batched_workload(seed=5, nmol=64, grids=(32, 40, 48), nrange=(8, 24)):
+    """Recipes of many small molecules (N_m ~ U{8..24}, n_m from ``grids``,
+    h = 0.4): per-launch work is small, so launch count and tail effects
+    dominate a per-molecule schedule."""
+    return batched_workload(seed=seed, nmol=nmol, grids=grids, nrange=nrange)

@@ -54,9 +54,20 @@ def test_committed_traffic_only_for_the_captured_sources():
     path = os.path.join(bench.ROOT, "profiles", "traffic.json")
     with open(path) as fh:
         d = json.load(fh)
-    entry = d[bench.WORKLOAD]["zconv"]
-    assert 0.85 <= entry["traffic_over_algorithmic"] <= 1.05
-    if entry["source_hash"] == bench.kernel_source_hash():
-        assert bench.committed_traffic("zconv") == entry["dram_bytes_per_launch"]
-    else:
-        assert bench.committed_traffic("zconv") is None
+    for wl in d:
+        for kern, entry in d[wl].items():
+            assert 0.85 <= entry["traffic_over_algorithmic"] <= 1.05, (wl, kern)
+            if entry["source_hash"] == bench.kernel_source_hash():
+                assert bench.committed_traffic(kern, wl) == entry["dram_bytes_per_launch"]
+            else:
+                assert bench.committed_traffic(kern, wl) is None
+
+
+def test_pair_sample_decode_and_cpu_model():
+    # sampled pair ids decode to (i, j), i <= j, in the row-major order of the
+    # pair energies
+    N = 37
+    order = [(i, j) for i in range(N) for j in range(i, N)]
+    for i, j, g in bench.sample_pairs(N, 50, seed=3):
+        assert order[g] == (i, j)
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()

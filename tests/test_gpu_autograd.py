@@ -3,10 +3,14 @@
 * FP64: central finite differences (step 1e-4) along 20 seeded directions
   normalised so that h^3 sum d^2 = 1 agree with <grad, d> to 1e-7 relative, and
   the gradient equals the oracle's 2 f_k h^3 (Vx psi)_k.
-* FP32: the gradient matches the FP64 gradient in relative L2 (1e-5).  On the
-  128-orbital 128^3 workload the FP32 energy is accurate to ~1e-8 relative, so
-  central differences at step 1e-4 carry ~1e-4 relative noise; that check uses
-  random localised directions (Gaussian bumps) and a 2e-3 bound.
+* FP32: the gradient matches the FP64 gradient in relative L2 (1e-5), also on
+  the 128-orbital 128^3 workload itself, where the FP64 gradient is the
+  analytic one of the FP64 path.  There the FP32 energy is accurate to ~1e-8
+  relative, so central differences at step 1e-4 carry ~1e-4 relative noise;
+  that check uses random localised directions (Gaussian bumps) and a 2e-3
+  bound.
+* The library's gradient (exx_gradient, the factor 2 f_k h^3 folded into the
+  accumulation) equals 2 f_k h^3 times exx_apply's action.
 """
 
 import math
@@ -100,6 +104,42 @@ def test_fp32_gradient_matches_fp64(env):
     assert np.linalg.norm(g32 - g64) <= 1e-5 * np.linalg.norm(g64)
     p64.close()
     p32.close()
+
+
+def test_library_gradient_is_scaled_action(env):
+    torch, dev, exx, ag = env
+    n, N, h = 16, 5, 0.45
+    psi_np = _orbitals(n, N, seed=74, h=h)
+    occ = np.array([2.0, 1.5, 1.0, 0.5, 0.25])
+    for prec in ("fp64", "fp32"):
+        plan = exx.ExxPlan(n, h, 0.25, occ, precision=prec, vx_fp64=True)
+        psi = torch.from_numpy(psi_np).to(dev, plan.dtype)
+        E1, vx = plan.apply(psi)
+        E2, g = plan.gradient(psi)
+        plan.close()
+        assert E1 == E2
+        sc = torch.as_tensor(2.0 * h ** 3 * occ, device=dev).view(-1, 1, 1, 1)
+        assert torch.allclose(g, sc * vx, rtol=1e-14, atol=0)
+
+
+def test_fp32_gradient_matches_fp64_on_the_128_orbital_workload(env):
+    # 128 orbitals on 128^3: FP32 autograd gradient against the FP64 path's
+    # analytic gradient 2 f_k h^3 (Vx psi)_k, relative L2 <= 1e-5
+    torch, dev, exx, ag = env
+    r, psi64 = synth.workload("c3_grad_n128_N128", dtype=np.float64, device=dev)
+    occ = np.full(r.norb, r.occupation)
+    p64 = exx.ExxPlan(r.n, r.h, r.alpha, occ, precision="fp64")
+    E64, g64 = p64.gradient(psi64)
+    p64.close()
+    p32 = exx.ExxPlan(r.n, r.h, r.alpha, occ, precision="fp32")
+    psi = psi64.float().requires_grad_(True)
+    E32 = ag.exx_energy(psi, p32)
+    E32.backward()
+    p32.close()
+    assert abs(float(E32.item()) - E64) <= 1e-6
+    num = float(torch.linalg.vector_norm(psi.grad.double() - g64).item())
+    den = float(torch.linalg.vector_norm(g64).item())
+    assert num <= 1e-5 * den, num / den
 
 
 def test_autograd_workload_128_orbitals_n128_fd(env):

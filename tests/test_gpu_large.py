@@ -1,6 +1,8 @@
-"""GPU parity at the large grids (n = 112, 128, 160; FP32) and on the
-512-orbital 160^3 cluster workload (sampled pair energies against the oracle,
-plus the identity E_x = 1/2 sum_i f_i h^3 <psi_i, (Vx psi)_i>)."""
+"""GPU parity at the large grids (n = 96, 112, 128, 160; FP32, element by
+element) and on the 512-orbital 160^3 cluster workload: sampled pair energies
+against the oracle, the identity E_x = 1/2 sum_i f_i h^3 <psi_i, (Vx psi)_i>,
+and, element by element over the whole grid, the contributions
+-alpha f_j V_ij psi_j of 64 sampled pairs to the exchange action."""
 
 import numpy as np
 import pytest
@@ -19,7 +21,7 @@ def env():
     return torch, torch.device("cuda:0"), exx
 
 
-@pytest.mark.parametrize("n,h", [(112, 0.4), (128, 0.37), (160, 0.42)])
+@pytest.mark.parametrize("n,h", [(96, 0.4), (112, 0.4), (128, 0.37), (160, 0.42)])
 def test_fp32_large_grids_against_oracle(env, n, h):
     torch, dev, exx = env
     r = synth.OrbitalRecipe(n=n, h=h, norb=2, nsites=3, seed=500 + n, gauss_per_orb=6,
@@ -61,3 +63,31 @@ def test_large_cluster_512_orbitals_n160(env):
         i, j = pairs[g]
         _, eo = o.exx_pair(psi[i].double().cpu().numpy(), psi[j].double().cpu().numpy(), Gh, r.h)
         assert abs(Eij[g] - eo) <= 1e-6 * max(1.0, abs(eo)), (i, j, Eij[g], eo)
+
+
+@pytest.mark.slow
+def test_large_cluster_pair_contributions_to_the_action(env):
+    # With f_j = 1 for one orbital j and f = 0 for all others, the action of
+    # every orbital i is (Vx psi)_i = -alpha V_ij psi_j: one plan over all
+    # 131,328 pairs gives each pair (i, j)'s contribution to the action, which
+    # is compared with the oracle's for 64 sampled i, element by element
+    torch, dev, exx = env
+    r, psi = synth.workload("c5_large_n160_N512", dtype=np.float32, device=dev)
+    j = 137
+    occ = np.zeros(r.norb)
+    occ[j] = 1.0
+    plan = exx.ExxPlan(r.n, r.h, r.alpha, occ, precision="fp32")
+    _, vx = plan.apply(psi)
+    plan.close()
+    Gh = o.kernel_spectrum(o.kernel_real_space(r.n, r.h))
+    pj = psi[j].double().cpu().numpy()
+    rng = np.random.default_rng(13)
+    worst = 0.0
+    for i in rng.choice(r.norb, size=64, replace=False):
+        V, _ = o.exx_pair(psi[i].double().cpu().numpy(), pj, Gh, r.h)
+        ref = -r.alpha * V * pj
+        got = vx[i].double().cpu().numpy()
+        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        worst = max(worst, err)
+        assert err <= 2e-6, (int(i), err)
+    assert worst > 0.0

@@ -288,6 +288,64 @@ def test_sharded_plans_sum_to_the_whole(torch_dev):
     full.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sharded_plans_against_oracle(torch_dev, prec):
+    # 2- and 3-way shards run one after the other on one GPU; the summed partial
+    # E_x, E_ij and Vx psi are compared with the oracle, not with the CUDA path
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    n, N, h = 16, 13, 0.45
+    psi_np = _orbitals(n, N, seed=62)
+    occ = np.linspace(0.5, 2.0, N)
+    Eo, vxo, Eijo = _oracle(psi_np, occ, 0.25, h)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    psi = torch.from_numpy(psi_np).to(dev, dt)
+    for R in (2, 3):
+        Es, vs, Eij = 0.0, None, np.zeros_like(Eijo)
+        for rank in range(R):
+            p = exx.ExxPlan(n, h, 0.25, occ, precision=prec, vx_fp64=True, tile=4)
+            p.set_shard(rank, R)
+            E, v = p.apply(psi)
+            Eij += p.pair_energies()  # other ranks' pairs read as zero
+            Es += E
+            vs = v if vs is None else vs + v
+            p.close()
+        vs = vs.cpu().numpy()
+        if prec == "fp64":
+            assert abs(Es - Eo) <= 1e-10 * abs(Eo)
+            assert np.max(np.abs(Eij - Eijo)) <= 1e-10 * np.max(np.abs(Eijo))
+            assert np.max(np.abs(vs - vxo)) <= 1e-10 * np.max(np.abs(vxo))
+        else:
+            assert abs(Es - Eo) <= 1e-6
+            assert np.max(np.abs(Eij - Eijo)) <= 1e-6
+            assert np.max(np.abs(vs - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+
+
+def test_dist_sharded_apply_nccl_against_oracle(torch_dev):
+    # dist.sharded_apply (shard + NCCL all-reduce of E_x and Vx psi) in a
+    # one-rank NCCL group on this GPU, against the oracle
+    import socket
+    import torch.distributed as tdist
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import dist as xdist, exx
+    n, N, h = 16, 9, 0.45
+    psi_np = _orbitals(n, N, seed=63)
+    occ = np.full(N, 2.0)
+    Eo, vxo, _ = _oracle(psi_np, occ, 0.25, h)
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    tdist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        plan = exx.ExxPlan(n, h, 0.25, occ, precision="fp64")
+        E, vx = xdist.sharded_apply(plan, torch.from_numpy(psi_np).to(dev))
+        plan.close()
+    finally:
+        tdist.destroy_process_group()
+    assert abs(E - Eo) <= 1e-10 * abs(Eo)
+    assert np.max(np.abs(vx.cpu().numpy() - vxo)) <= 1e-10 * np.max(np.abs(vxo))
+
+
 def test_screened_erfc_kernel(torch_dev):
     # screened hybrids: only the Poisson filter changes (HSE-type erfc(w r)/r)
     psi = _orbitals(12, 3, seed=33)
