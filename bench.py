@@ -430,11 +430,16 @@ def batched_record(torch, dev, exx, synth, ag, recipes, label, fp64=True):
     b.graph(True)
     s = torch.cuda.Stream()
     E = torch.zeros(len(mols), dtype=torch.float64, device=dev)
-    with torch.cuda.stream(s):
-        for _ in range(2):
-            b.gradient(E, stream=s)
-        ms = cuda_time(torch, s, lambda: b.gradient(E, stream=s), 3)
-    info = b.info()
+    modes = {}
+    for mode in ("waves", "persistent"):  # graph of per-wave launches / one persistent launch per group
+        b.persistent(mode == "persistent")
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                b.gradient(E, stream=s)
+            modes[mode] = (cuda_time(torch, s, lambda: b.gradient(E, stream=s), 3), b.info())
+    best = min(modes, key=lambda k: modes[k][0])
+    b.persistent(best == "persistent")
+    ms, info = modes[best]
     # batched autograd: ExxBatchEnergy forward + backward
     xs = [p.clone().requires_grad_(True) for p in p32]
 
@@ -459,8 +464,10 @@ def batched_record(torch, dev, exx, synth, ag, recipes, label, fp64=True):
     for pl in plans:
         pl.close()
     rec = {"workload": label, "pairs": pairs, "ms_per_step": ms, "value": pairs / (ms * 1e-3),
-           "unit": UNIT, "graph": True, "groups": info["groups"], "waves": info["waves"],
-           "launches_per_step": info["launches_apply"],
+           "unit": UNIT, "graph": True, "schedule": best, "groups": info["groups"],
+           "waves": info["waves"], "launches_per_step": info["launches_apply"],
+           "schedules": {k: {"ms_per_step": v[0], "launches_per_step": v[1]["launches_apply"]}
+                         for k, v in modes.items()},
            "autograd_ms_per_step": ms_ag,
            "sequential_plans_ms": ms_seq, "speedup_vs_sequential_plans": ms_seq / ms}
     if fp64:

@@ -347,6 +347,22 @@ exx_status_t exx_batch_gradient(exx_batch_t batch, double* E_dev, void* cuda_str
  */
 exx_status_t exx_batch_graph(exx_batch_t batch, int enable);
 
+/*
+ * exx_batch_set_persistent -- enable (1) or disable (0) the persistent
+ * schedule: each group of molecules with the same (n, h) runs as ONE launch of
+ * a persistent kernel that takes the (wave, pass, unit) items of all its pair
+ * tiles from a device work queue, instead of five launches per wave.  Items of
+ * a pass wait (bounded, on the device) for the items they depend on: a wait
+ * that runs out sets the flag that exx_batch_pair_energies reports as
+ * EXX_ERR_TIMEOUT, and the rest of the launch is skipped.  Results equal those
+ * of the launch-per-pass schedule bit for bit.  FP32 grids whose slab kernels
+ * run as CTA clusters (n = 160) keep the launch-per-pass schedule.  The first
+ * enable builds the queue tables, allocates a second workspace slot if the
+ * batch has none (returns EXX_ERR_OOM if that fails) and synchronises the
+ * stream; it discards captured graphs.
+ */
+exx_status_t exx_batch_set_persistent(exx_batch_t batch, int enable, void* cuda_stream);
+
 /* exx_batch_pair_energies -- pair energies of molecule mol (order as in
  * exx_pair_energies) of the last call, to host memory; synchronises. */
 exx_status_t exx_batch_pair_energies(exx_batch_t batch, int mol, double* out_host,

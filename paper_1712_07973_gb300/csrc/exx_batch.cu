@@ -96,6 +96,11 @@ struct Group {
   void* Gs = nullptr;
   void* tw = nullptr;
   CUtensorMap gmap{};  // TMA descriptor of Gs (ops->stage_table)
+  // persistent mode: the group's queue segments (offset into the batch's
+  // segment table and count, per mode: 0 apply or gradient, 1 energy), items,
+  // and accumulation point blocks per tile
+  int seg_off[2] = {0, 0}, nseg[2] = {0, 0}, total[2] = {0, 0};
+  int nblk = 0;
 };
 
 struct Mol {
@@ -146,6 +151,13 @@ struct exx_batch_s {
   cudaEvent_t ev_fork = nullptr, ev_done[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // graph capture
   bool graph_on = false;
+  // persistent mode (exx_batch_set_persistent): queue segments of every group,
+  // their device copy and the queue counters
+  bool persistent = false;
+  std::vector<QSeg> segs;
+  QSeg* d_segs = nullptr;
+  int* d_qc = nullptr;
+  int qc_len = 0;
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // [apply, energy, gradient]
   double* gE[3] = {nullptr, nullptr, nullptr};
   cudaStream_t gstream[3] = {nullptr, nullptr, nullptr};
@@ -157,7 +169,7 @@ namespace {
 void batch_free(exx_batch_t b) {
   void* ptrs[] = {b->d_pairs, b->d_tiles, b->d_occ,  b->Epair,           b->epart,
                   b->X,       b->V,       b->vacc,   b->d_mt,            (void*)b->d_psi_tab,
-                  b->d_vacc_tab, b->d_vx_tab, b->d_count, b->d_err};
+                  b->d_vacc_tab, b->d_vx_tab, b->d_count, b->d_err, b->d_segs, b->d_qc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (Group& g : b->groups) {
@@ -189,6 +201,78 @@ template <typename T> bool balloc(exx_batch_t b, T** p, size_t bytes) {
 
 // apply: Vx psi (grad = false) or the gradient 2 f_k h^3 (Vx psi)_k (grad =
 // true) into the bound outputs
+// Queue segments of a group for the persistent kernel (order and
+// prerequisites in exx_persist.cuh); indices are relative to the group's
+// first segment.  stall: test hook, one extra segment that never completes is
+// made a prerequisite of the first zconv segment.
+void build_segments(exx_batch_t b, Group& g, bool apply, bool stall, std::vector<QSeg>& out) {
+  const int n = g.n, W = (int)g.waves.size();
+  const int NWP = g.ops->persist_nt / 32;
+  const long long n3 = (long long)n * n * n;
+  g.nblk = (int)((n3 + g.ops->persist_nt - 1) / g.ops->persist_nt);
+  std::vector<int> idx((size_t)W * 5, -1);
+  std::vector<QSeg> v;
+  int cursor = 0;
+  const int passes_apply[5] = {P_FWD, P_ZCONV, P_ENERGY, P_INV, P_ACCUM};
+  const int np = apply ? 5 : 3;
+  for (int w0 = 0; w0 < W; w0 += 2)
+    for (int k = 0; k < np; ++k)
+      for (int w = w0; w < std::min(W, w0 + 2); ++w) {
+        const int ps = passes_apply[k];
+        const Wave& wv = g.waves[w];
+        QSeg q;
+        q.start = cursor;
+        q.pass = ps;
+        q.slot = w % 2;
+        q.pair_off = wv.pair_off;
+        q.npair = wv.npair;
+        q.tile_off = wv.tile_off;
+        q.ntile = wv.ntile;
+        q.nunits = ps == P_FWD || ps == P_INV ? wv.npair * n
+                   : ps == P_ZCONV            ? wv.npair * (n + 1) * g.ops->nyb
+                   : ps == P_ENERGY           ? (wv.npair + NWP - 1) / NWP
+                                              : wv.ntile * g.nblk;
+        // units per item: small grids take several, so that the per-item queue
+        // work (counter, barriers, release) stays small against the transforms
+        q.per = (ps == P_FWD || ps == P_INV || ps == P_ZCONV) ? (n <= 48 ? 4 : n <= 80 ? 2 : 1) : 1;
+        q.nitems = (q.nunits + q.per - 1) / q.per;
+        q.dep[0] = q.dep[1] = q.dep[2] = -1;
+        auto at = [&](int ww, int pp) { return ww >= 0 ? idx[(size_t)ww * 5 + pp] : -1; };
+        if (ps == P_FWD) {
+          q.dep[0] = at(w - 2, apply ? P_INV : P_ZCONV);  // its workspace slot is free
+        } else if (ps == P_ZCONV) {
+          q.dep[0] = at(w, P_FWD);
+          q.dep[1] = at(w - 2, P_ENERGY);  // energy partials of the slot read
+        } else if (ps == P_ENERGY) {
+          q.dep[0] = at(w, P_ZCONV);
+        } else if (ps == P_INV) {
+          q.dep[0] = at(w, P_ZCONV);
+          q.dep[1] = at(w - 2, P_ACCUM);  // potentials of the slot read
+        } else {
+          q.dep[0] = at(w, P_INV);
+          q.dep[1] = at(w - 1, P_ACCUM);  // accumulation in tile order
+        }
+        idx[(size_t)w * 5 + ps] = (int)v.size();
+        v.push_back(q);
+        cursor += q.nitems;
+      }
+  const int m = apply ? 0 : 1;
+  g.total[m] = cursor;
+  if (stall) {  // never completes: no item maps to it
+    QSeg q{};
+    q.start = cursor;
+    q.nunits = q.nitems = q.per = 1;
+    q.pass = P_FWD;
+    q.dep[0] = q.dep[1] = q.dep[2] = -1;
+    v[idx[P_ZCONV]].dep[2] = (int)v.size();
+    v.push_back(q);
+  }
+  g.seg_off[m] = (int)out.size();
+  g.nseg[m] = (int)v.size();
+  out.insert(out.end(), v.begin(), v.end());
+  (void)b;
+}
+
 exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, bool grad, cudaStream_t st) {
   if (apply) {
     long long tot = 0;
@@ -197,7 +281,9 @@ exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, bool grad, cudaSt
   }
   // two lanes: consecutive waves alternate between two streams with their own
   // workspaces; the accumulation stays on st in wave order
-  const int nl = b->lanes;
+  // persistent mode: one launch per group that supports it, all on st (the
+  // queue uses both workspace slots, so no lanes)
+  const int nl = b->persistent ? 1 : b->lanes;
   if (nl > 1) {
     if (cudaEventRecord(b->ev_fork, st) != cudaSuccess) return EXX_ERR_CUDA;
     for (int l = 0; l < nl; ++l)
@@ -210,6 +296,39 @@ exx_status_t enqueue(exx_batch_t b, double* E_dev, bool apply, bool grad, cudaSt
   int k = 0;
   for (const Group& g : b->groups) {
     const long long n3 = (long long)g.n * g.n * g.n;
+    if (b->persistent && g.ops->persist_ok) {
+      const int m = apply ? 0 : 1;
+      if (cudaMemsetAsync(b->d_qc, 0, (size_t)(g.nseg[m] + 2) * sizeof(int), st) != cudaSuccess)
+        return EXX_ERR_CUDA;
+      PersistArgs a{};
+      a.psi_tab = b->d_psi_tab;
+      a.pairs = b->d_pairs;
+      a.tiles = b->d_tiles;
+      a.segs = b->d_segs + g.seg_off[m];
+      a.nseg = g.nseg[m];
+      a.total = g.total[m];
+      a.X[0] = static_cast<float2*>(b->X);
+      a.X[1] = static_cast<float2*>(b->X_2);
+      a.V[0] = static_cast<float*>(b->V);
+      a.V[1] = static_cast<float*>(b->V_2);
+      a.epart[0] = b->epart;
+      a.epart[1] = b->epart2;
+      a.Gs = static_cast<const float*>(g.Gs);
+      a.tw = static_cast<const float2*>(g.tw);
+      a.Epair = b->Epair;
+      a.vx_tab = b->d_vacc_tab;
+      a.occ = b->d_occ;
+      a.qc = b->d_qc;
+      a.err = b->d_err;
+      a.h3 = g.h * g.h * g.h;
+      a.n3 = n3;
+      a.nblk = g.nblk;
+      a.grad = grad ? 1 : 0;
+      a.energy_only = apply ? 0 : 1;
+      a.vec2 = (b->vec2 && (n3 % 2) == 0) ? 1 : 0;
+      if (g.ops->persist(a, st) != cudaSuccess) return EXX_ERR_CUDA;
+      continue;
+    }
     const int nper = (g.n + 1) * g.ops->nyb;
     const double h3 = g.h * g.h * g.h;
     for (const Wave& w : g.waves) {
@@ -576,6 +695,61 @@ exx_status_t exx_batch_energy(exx_batch_t b, double* E_dev, void* cuda_stream) {
   return run_batch(b, E_dev, false, false, static_cast<cudaStream_t>(cuda_stream));
 }
 
+exx_status_t exx_batch_set_persistent(exx_batch_t b, int enable, void* cuda_stream) {
+  if (b == nullptr) return EXX_ERR_INVALID_ARG;
+  if ((enable != 0) == b->persistent) return EXX_OK;
+  for (int k = 0; k < 3; ++k)  // the captured graphs embed the schedule
+    if (b->gexec[k]) {
+      cudaGraphExecDestroy(b->gexec[k]);
+      b->gexec[k] = nullptr;
+    }
+  if (!enable) {
+    b->persistent = false;
+    return EXX_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (b->d_segs == nullptr) {
+    const char* hook = std::getenv("EXX_TEST_STALL_QUEUE");
+    const bool stall = hook != nullptr && hook[0] == '1';
+    std::vector<QSeg> segs;
+    int mx = 0;
+    for (Group& g : b->groups)
+      if (g.ops->persist_ok) {
+        build_segments(b, g, true, stall, segs);
+        build_segments(b, g, false, stall, segs);
+        mx = std::max(mx, std::max(g.nseg[0], g.nseg[1]));
+      }
+    if (segs.empty()) return EXX_OK;  // no group has a persistent kernel
+    // the queue reuses two workspace slots (those of the two pipeline lanes)
+    if (b->X_2 == nullptr) {
+      if (!balloc(b, &b->epart2, b->ep_bytes) || !balloc(b, &b->X_2, b->x_bytes) ||
+          !balloc(b, &b->V_2, b->v_bytes))
+        return EXX_ERR_OOM;
+    }
+    if (!balloc(b, &b->d_segs, segs.size() * sizeof(QSeg)) ||
+        !balloc(b, &b->d_qc, (size_t)(mx + 2) * sizeof(int)))
+      return EXX_ERR_OOM;
+    b->qc_len = mx + 2;
+    if (cudaMemcpyAsync(b->d_segs, segs.data(), segs.size() * sizeof(QSeg), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return EXX_ERR_CUDA;
+    }
+    b->segs.swap(segs);
+  }
+  for (const Group& g : b->groups)  // function attributes and grid size, outside any capture
+    if (g.ops->persist_ok) {
+      PersistArgs none{};
+      if (g.ops->persist(none, st) != cudaSuccess) {
+        cudaGetLastError();
+        return EXX_ERR_CUDA;
+      }
+    }
+  b->persistent = true;
+  return EXX_OK;
+}
+
 exx_status_t exx_batch_graph(exx_batch_t b, int enable) {
   if (b == nullptr) return EXX_ERR_INVALID_ARG;
   b->graph_on = enable != 0;
@@ -609,7 +783,12 @@ exx_status_t exx_batch_info(exx_batch_t b, int* ngroups, int* nwaves, size_t* wo
   if (ngroups) *ngroups = (int)b->groups.size();
   if (nwaves) *nwaves = nw;
   if (workspace_bytes) *workspace_bytes = b->ws;
-  if (launches_apply) *launches_apply = 5 * nw + 2;
+  if (launches_apply) {
+    int la = 2;  // E_x totals and the conversion of the outputs
+    for (const Group& g : b->groups)
+      la += (b->persistent && g.ops->persist_ok) ? 1 : 5 * (int)g.waves.size();
+    *launches_apply = la;
+  }
   if (pairs) *pairs = (long long)b->pairs.size();
   return EXX_OK;
 }

@@ -23,7 +23,7 @@
 // Layouts: psi[o][z][y][x]; X[p][kx][z][ky] complex; V[p][z][y][x].
 // With periodic boundary conditions (template flag PER) the grid has 2n points
 // per axis, the lines are not padded and no transform is pruned; large slabs
-// are split over two-CTA clusters (CL = 2).  Mixed boundary conditions give
+// are split over clusters of CL = 2 or 4 CTAs.  Mixed boundary conditions give
 // zconv a z line of its own (NZ, PERZ): slab = periodic x, y with a free z;
 // wire = free x, y with a periodic z.
 #pragma once
@@ -65,6 +65,14 @@ template <int L1, int L2> struct Scr {
 };
 
 template <typename R> __device__ __forceinline__ R sq(R a) { return a * a; }
+
+// Load of data that other CTAs of the same launch may have written (COH, the
+// persistent batched kernel: through L2, never a stale L1 or read-only-cache
+// line); plain load otherwise.
+template <bool COH, typename T> __device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
 
 // Line transforms of the two boundary conditions: free (zero-padded line of
 // length 2n, second half of the input zero, second half of the inverse output
@@ -160,17 +168,22 @@ template <typename C> EXX_HD void split_step(C zk, C zm, C w, C& xk, C& xm) {
 // Hermitian half spectrum X[k], k = 0..n (row n is the Nyquist row).  y: the
 // pruned length-2n FFT per kx row, written to HBM as X[p][kx][z][ky].  Q = 0:
 // warp-owned y passes (two rows per warp); Q > 0: CTA-wide batches of Q rows.
-// CL = 2 (large grids): a cluster of two CTAs per (z-slab, pair), CTA c holding
-// the columns y in [c n/2, (c+1) n/2) of every row; the x passes stay local,
-// the y passes of a CTA's rows read the other half of each row from the peer's
-// shared memory (distributed shared memory).
+// CL = 2 or 4 (large grids): a cluster of CL CTAs per (z-slab, pair), CTA c
+// holding the columns y in [c n/CL, (c+1) n/CL) of every row; the x passes stay
+// local, the y passes of a CTA's rows read the other parts of each row from the
+// peers' shared memory (distributed shared memory).
 // PER: periodic boundary conditions: the grid has G = 2n points per axis, the
 // lines are not padded and nothing is pruned (N is then half the grid).
-template <typename R, int N, int NT, int MINB, int Q, int CL, bool PER>
-__global__ void __launch_bounds__(NT, MINB)
-k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
-         const int4* __restrict__ pairs, cplx<R>* __restrict__ X, const cplx<R>* __restrict__ tw_g,
-         long long n3) {
+// fwd_xy_unit: the work of one CTA, bx = z-slab * CL + cluster rank, p = pair
+// slot; k_fwd_xy launches one per block, the persistent batched kernel takes
+// them from its work queue.
+template <typename R, int N, int NT, int Q, int CL, bool PER>
+__device__ __forceinline__ void fwd_xy_unit(const R* __restrict__ psi0,
+                                            const R* const* __restrict__ psi_tab,
+                                            const int4* __restrict__ pairs,
+                                            cplx<R>* __restrict__ X,
+                                            const cplx<R>* __restrict__ tw_g, long long n3,
+                                            const int bx, const int p) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int X1 = split_x(N), X2 = N / X1;
@@ -180,7 +193,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   constexpr int NIN = PER ? L1 : H1;  // nonzero inputs of the y pass-1 DFTs
   constexpr int NY = G / CL, SP = NY + 1;
   constexpr int NB = CL == 1 ? L1 : NY / L2;  // y = L2 n1 + n2 lies in half n1 / NB
-  static_assert(CL == 1 || (Q == 0 && G % 2 == 0 && NY % L2 == 0), "cluster split");
+  static_assert(CL == 1 || (Q == 0 && G % CL == 0 && NY % L2 == 0), "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // twiddle tables (packed layout of build_twiddles): TY[k1][n2] = w^(n2 k1)
   // for the y pass and TX[k1][n2] = w^(2 n2 k1) for the x pass, so that
@@ -190,9 +203,8 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   C* Sl = tx + N;  // slab, rows srow(r)
 
   const int tid = threadIdx.x;
-  const int z = blockIdx.x / CL, c = blockIdx.x % CL;  // c: rank in the cluster
+  const int z = bx / CL, c = bx % CL;  // c: rank in the cluster
   const int y0 = c * NY;
-  const int p = blockIdx.y;
   const int4 pr = pairs[p];  // (i, j, pair id, molecule slot)
   const R* psi = psi_tab ? psi_tab[pr.w] : psi0;
   const R* __restrict__ pi = psi + (long long)pr.x * n3 + (long long)z * G * G;
@@ -241,12 +253,19 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   __syncthreads();
   // split: X[k] = E[k] + w^k O[k], X[n-k] = conj(E[k] - w^k O[k]), with
   // E = (Z[k] + conj Z[n-k]) / 2, O = (Z[k] - conj Z[n-k]) / (2i), w = omega_2n
+  // Q = 0: the two real rows kx = 0 and kx = n travel as one complex row
+  // X[0] + i X[n] through the y pass (MERGE), which splits them again
+  constexpr bool MERGE = Q == 0;
   for (int u = tid; u < NY * (N / 2 + 1); u += NT) {
     const int k = u / NY, y = u - k * NY;
     if (k == 0) {
       const C z0 = Sl[y];
-      Sl[y] = mkc<C>(z0.x + z0.y, R(0));
-      Sl[srow<SP, X1>(N) + y] = mkc<C>(z0.x - z0.y, R(0));
+      if constexpr (MERGE) {
+        Sl[y] = mkc<C>(z0.x + z0.y, z0.x - z0.y);
+      } else {
+        Sl[y] = mkc<C>(z0.x + z0.y, R(0));
+        Sl[srow<SP, X1>(N) + y] = mkc<C>(z0.x - z0.y, R(0));
+      }
     } else if (2 * k == N) {
       const C zk = Sl[srow<SP, X1>(k) + y];
       Sl[srow<SP, X1>(k) + y] = mkc<C>(zk.x, -zk.y);
@@ -259,17 +278,16 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
       *rm = xm;
     }
   }
-  // the two halves of each row (columns below / above n/2): with CL = 2 this
-  // CTA's slab and the peer's
-  const C* h0 = Sl;
-  const C* h1 = Sl;
-  if constexpr (CL == 2) {
+  // the CL parts of each row (columns [q n/CL, (q+1) n/CL) in CTA q of the
+  // cluster): this CTA's slab and its peers'
+  const C* hp[CL];
+  if constexpr (CL > 1) {
     cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-    const C* peer = cl.map_shared_rank(Sl, c ^ 1);
-    h0 = c == 0 ? Sl : peer;
-    h1 = c == 0 ? peer : Sl;
-    cl.sync();  // both halves transformed along x
+#pragma unroll
+    for (int q = 0; q < CL; ++q) hp[q] = q == c ? Sl : cl.map_shared_rank(Sl, q);
+    cl.sync();  // every part transformed along x
   } else {
+    hp[0] = Sl;
     __syncthreads();
   }
   // y: pruned length-2n FFT per kx row; pass 1 (DFT_L1 over n1 < L1/2, then
@@ -291,14 +309,15 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 #pragma unroll
       for (int k1 = 1; k1 < L1; ++k1) twr[k1] = cl16 < L2 ? ty[k1 * L2 + cl16] : mkc<C>(R(0), R(0));
     }
-    for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 <= N; r0 += 2 * NWP * CL) {
+    // rows kx < n (row 0 carries rows 0 and n): 2n/(two rows per warp) rounds
+    for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 < N; r0 += 2 * NWP * CL) {
       const int kx = r0 + hr;
-      const bool rv = kx <= N;
+      const bool rv = kx < N;
       const int rb = srow<SP, X1>(kx);
       if (rv && cl16 < L2) {
         C v[L1];
 #pragma unroll
-        for (int n1 = 0; n1 < NIN; ++n1) v[n1] = (n1 < NB ? h0 : h1)[rb + L2 * (n1 % NB) + cl16];
+        for (int n1 = 0; n1 < NIN; ++n1) v[n1] = hp[n1 / NB][rb + L2 * (n1 % NB) + cl16];
         dft_fwd_in<L1, PER>(v);
         C* o = Sw + cl16 * Scr<L1, L2>::row;
         o[0] = v[0];
@@ -309,7 +328,7 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
         if (rv) {
           C v[L1];
 #pragma unroll
-          for (int n1 = 0; n1 < NIN; ++n1) v[n1] = (n1 < NB ? h0 : h1)[rb + L2 * (n1 % NB) + n2];
+          for (int n1 = 0; n1 < NIN; ++n1) v[n1] = hp[n1 / NB][rb + L2 * (n1 % NB) + n2];
           dft_fwd_in<L1, PER>(v);
           C* o = Sw + n2 * Scr<L1, L2>::row;
           o[0] = v[0];
@@ -325,13 +344,33 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
         for (int n2 = 0; n2 < L2; ++n2) v[n2] = q[n2 * Scr<L1, L2>::row];
         dft<L2, 1, -1>(v);
         C* out = X + (((long long)p * (N + 1) + kx) * G + z) * L + cl16;
+        if (kx == 0) {
+          // split C = Y0 + i YN (Y0, YN spectra of real rows):
+          // Y0[k] = (C[k] + conj C[-k]) / 2, YN[k] = (C[k] - conj C[-k]) / (2i).
+          // C[k1 + L1 k2] is v[k2] of lane k1; C[-k] is v[(L2 - k2) % L2] of
+          // lane 0 for k1 = 0, else v[L2 - 1 - k2] of lane L1 - k1.
+          const unsigned mask = (1u << L1) - 1u;  // lanes 0..L1-1 of half warp 0
+          const int partner = (L1 - cl16) % L1;
+          C* outN = X + (((long long)p * (N + 1) + N) * G + z) * L + cl16;
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
+          for (int k2 = 0; k2 < L2; ++k2) {
+            C b;
+            b.x = __shfl_sync(mask, v[L2 - 1 - k2].x, partner, 16);
+            b.y = __shfl_sync(mask, v[L2 - 1 - k2].y, partner, 16);
+            if (cl16 == 0) b = v[(L2 - k2) % L2];
+            const C a = v[k2];
+            out[L1 * k2] = mkc<C>(R(0.5) * (a.x + b.x), R(0.5) * (a.y - b.y));
+            outN[L1 * k2] = mkc<C>(R(0.5) * (a.y + b.y), R(0.5) * (b.x - a.x));
+          }
+        } else {
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) out[L1 * k2] = v[k2];
+        }
       }
       __syncwarp();
     }
-    // the peer may still be reading this CTA's half
-    if constexpr (CL == 2) cooperative_groups::this_cluster().sync();
+    // the peers may still be reading this CTA's part
+    if constexpr (CL > 1) cooperative_groups::this_cluster().sync();
   } else {
     // CTA-wide batches of Q rows
     for (int r0 = 0; r0 <= N; r0 += Q) {
@@ -367,6 +406,18 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
   }
 }
 
+template <typename R, int N, int NT, int MINB, int Q, int CL, bool PER>
+__global__ void __launch_bounds__(NT, MINB)
+k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
+         const int4* __restrict__ pairs, cplx<R>* __restrict__ X, const cplx<R>* __restrict__ tw_g,
+         long long n3) {
+  // grid (CL * pairs, z): the CTAs of one z-slab for all pairs of the tile run
+  // together, so the tile's orbital planes at that z are read from L2 once
+  // they are in (at 160^3 the tile's orbitals, 262 MB, exceed L2)
+  fwd_xy_unit<R, N, NT, Q, CL, PER>(psi0, psi_tab, pairs, X, tw_g, n3,
+                                    blockIdx.y * CL + blockIdx.x % CL, blockIdx.x / CL);
+}
+
 // ------------------------------------------------------------------- zconv
 // One CTA per (32 consecutive ky columns, kx, pair); lane = column, warps
 // share the sub-DFTs of each pass.  Along z: pruned forward FFT (pass 1 of
@@ -383,11 +434,14 @@ k_fwd_xy(const R* __restrict__ psi0, const R* const* __restrict__ psi_tab,
 // transform (length 2NZ, tw_g its twiddles); they differ for the mixed
 // boundary conditions: slab (x, y periodic, z free) and wire (x, y free,
 // z periodic).
+// zconv_unit: the work of one CTA (yb = column block, kx, p = pair slot).
 template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool PER, bool ENERGY_ONLY,
-          int NZ = N, bool PERZ = PER>
-__global__ void __launch_bounds__(32 * NW, MINB)
-k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
-        double* __restrict__ epart, const __grid_constant__ CUtensorMap gmap, int* __restrict__ err) {
+          int NZ, bool PERZ, bool COH>
+__device__ __forceinline__ void zconv_unit(cplx<R>* __restrict__ X, const R* __restrict__ Gs,
+                                           const cplx<R>* __restrict__ tw_g,
+                                           double* __restrict__ epart, const CUtensorMap* gmap,
+                                           int* __restrict__ err, const int yb, const int kx,
+                                           const int p) {
   using C = cplx<R>;
   constexpr int LY = 2 * N;  // ky extent: the row stride of X and of the kernel table
   constexpr int L = 2 * NZ, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
@@ -407,7 +461,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   __shared__ __align__(8) unsigned long long gbar;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int yb = blockIdx.x, kx = blockIdx.y, p = blockIdx.z;
+  constexpr int NYB = (LY + W - 1) / W;  // column blocks per kx plane
   const int ky = yb * W + lane;
   const bool valid = lane < W && ky < LY;
   if constexpr (STAGE) {
@@ -418,7 +472,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
         // test hook: no copy, nothing arrives, the wait below runs out
       } else if ((smem_u32(gsm) & 127u) == 0) {
         mbar_expect_tx(&gbar, (unsigned)(L * W * sizeof(R)));
-        tma_load_3d(gsm, &gmap, yb * W, 0, kx, &gbar);
+        tma_load_3d(gsm, gmap, yb * W, 0, kx, &gbar);
       } else {  // never expected: report instead of issuing an unaligned copy
         atomicExch(err, 2);
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&gbar)) : "memory");
@@ -446,7 +500,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
     C v[L1];
 #pragma unroll
     for (int n1 = 0; n1 < NIN; ++n1)
-      v[n1] = valid ? col[(long long)(L2 * n1 + n2) * LY] : mkc<C>(R(0), R(0));
+      v[n1] = valid ? ldx<COH>(col + (long long)(L2 * n1 + n2) * LY) : mkc<C>(R(0), R(0));
     dft_fwd_in<L1, PERZ>(v);
     if (lane < W) {
       buf[(n2 * L1) * W + lane] = v[0];
@@ -464,7 +518,7 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
   double eacc = 0.0;
   // PF (unstaged, with the register budget of two CTAs per SM): the unit's
   // kernel-table values are requested before its transform
-  constexpr bool PF = !STAGE && MINB <= 2 && sizeof(R) == 4;
+  constexpr bool PF = !STAGE && sizeof(R) == 4 && 65536 / (32 * NW * MINB) >= 96;
   for (int k1 = warp; k1 < L1; k1 += NW) {
     R gp[PF ? L2 : 1];
     if constexpr (PF) {
@@ -523,8 +577,19 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 #pragma unroll
     for (int w = 0; w < NW; ++w) s += red[w];
     const double wk = (kx == 0 || kx == N) ? 1.0 : 2.0;
-    epart[((long long)p * M + kx) * gridDim.x + yb] = wk * s;
+    epart[((long long)p * M + kx) * NYB + yb] = wk * s;
   }
+}
+
+template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool PER, bool ENERGY_ONLY,
+          int NZ = N, bool PERZ = PER>
+__global__ void __launch_bounds__(32 * NW, MINB)
+k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
+        double* __restrict__ epart, const __grid_constant__ CUtensorMap gmap, int* __restrict__ err) {
+  // grid (pairs, column blocks, kx): consecutive CTAs read the same kernel-table
+  // slice, which then comes from L2 for all pairs of the tile
+  zconv_unit<R, N, NW, MINB, STAGE, FOLDY, PER, ENERGY_ONLY, NZ, PERZ, false>(
+      X, Gs, tw_g, epart, &gmap, err, blockIdx.y, blockIdx.z, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ inv_yx
@@ -534,12 +599,15 @@ k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __rest
 // Z[k] = E'[k] + i O'[k] (E' = X[k] + conj X[n-k], O' = (X[k] - conj X[n-k])
 // w^-k), whose inverse FFT (in place in column y) gives the even and odd
 // samples of the real line: V[2m] = Re, V[2m+1] = Im, kept for x < n.
-// CL = 2: two-CTA cluster as in fwd_xy; a CTA's y passes write the other half
-// of each row into the peer's slab, then each CTA transforms its own columns.
+// CL = 2 or 4: CTA cluster as in fwd_xy; a CTA's y passes write the other
+// parts of each row into the peers' slabs, then each CTA transforms its own
+// columns.
 // PER: periodic boundary conditions (see fwd_xy).
-template <typename R, int N, int NT, int MINB, int Q, int CL, bool PER>
-__global__ void __launch_bounds__(NT, MINB)
-k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __restrict__ tw_g) {
+// inv_yx_unit: the work of one CTA (bx = z-slab * CL + cluster rank, p = pair).
+template <typename R, int N, int NT, int Q, int CL, bool PER, bool COH>
+__device__ __forceinline__ void inv_yx_unit(const cplx<R>* __restrict__ X, R* __restrict__ V,
+                                            const cplx<R>* __restrict__ tw_g, const int bx,
+                                            const int p) {
   using C = cplx<R>;
   constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int X1 = split_x(N), X2 = N / X1;
@@ -549,27 +617,25 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   constexpr int NOUT = PER ? L1 : H1;  // kept outputs of the y pass-2 DFTs
   constexpr int NY = G / CL, SP = NY + 1;
   constexpr int NB = CL == 1 ? L1 : NY / L2;  // y = L2 m1 + m2 lies in half m1 / NB
-  static_assert(CL == 1 || (Q == 0 && G % 2 == 0 && NY % L2 == 0), "cluster split");
+  static_assert(CL == 1 || (Q == 0 && G % CL == 0 && NY % L2 == 0), "cluster split");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);  // w^k, high parts [L]
   C* ti = tw + L;                          // TI[m2][k1] = w^(m2 k1) [L] (see fwd_xy)
   C* Sl = ti + L;                          // slab, rows srow(r) (see fwd_xy)
 
   const int tid = threadIdx.x;
-  const int z = blockIdx.x / CL, c = blockIdx.x % CL;  // c: rank in the cluster
+  const int z = bx / CL, c = bx % CL;  // c: rank in the cluster
   const int y0 = c * NY;
-  const int p = blockIdx.y;
   for (int t = tid; t < L; t += NT) tw[t] = tw_g[t];
   for (int t = tid; t < L; t += NT) ti[t] = tw_g[2 * L + N + t];
-  C* h0 = Sl;  // row halves (see fwd_xy)
-  C* h1 = Sl;
-  if constexpr (CL == 2) {
+  C* hp[CL];  // row parts (see fwd_xy)
+  if constexpr (CL > 1) {
     cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
-    C* peer = cl.map_shared_rank(Sl, c ^ 1);
-    h0 = c == 0 ? Sl : peer;
-    h1 = c == 0 ? peer : Sl;
-    cl.sync();  // the peer has started (its shared memory may be written)
+#pragma unroll
+    for (int q = 0; q < CL; ++q) hp[q] = q == c ? Sl : cl.map_shared_rank(Sl, q);
+    cl.sync();  // the peers have started (their shared memory may be written)
   } else {
+    hp[0] = Sl;
     __syncthreads();
   }
   // y: inverse length-2n FFT per kx row keeping y < n; pass 1 (DFT_L2 over
@@ -590,14 +656,24 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
 #pragma unroll
       for (int m2 = 1; m2 < L2; ++m2) twr[m2] = cl16 < L1 ? ti[m2 * L1 + cl16] : mkc<C>(R(0), R(0));
     }
-    for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 <= N; r0 += 2 * NWP * CL) {
+    // rows kx < n; row 0 transforms X[0] + i X[n]: both give real lines
+    // (Hermitian in ky), which come out as the real and imaginary parts
+    for (int r0 = 2 * (c * NWP + (tid >> 5)); r0 < N; r0 += 2 * NWP * CL) {
       const int kx = r0 + hr;
-      const bool rv = kx <= N;
+      const bool rv = kx < N;
       if (rv && cl16 < L1) {
         const C* in = X + (((long long)p * (N + 1) + kx) * G + z) * L + cl16;
         C v[L2];
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
+        for (int k2 = 0; k2 < L2; ++k2) v[k2] = ldx<COH>(in + L1 * k2);
+        if (kx == 0) {
+          const C* inN = X + (((long long)p * (N + 1) + N) * G + z) * L + cl16;
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) {
+            const C w = ldx<COH>(inN + L1 * k2);
+            v[k2] = mkc<C>(v[k2].x - w.y, v[k2].y + w.x);
+          }
+        }
         dft<L2, 1, 1>(v);
         C* q = Sw + cl16;
         q[0] = v[0];
@@ -615,12 +691,12 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
           dft_inv_out<L1, PER>(v);
           const int rb = srow<SP, X1>(kx);
 #pragma unroll
-          for (int m1 = 0; m1 < NOUT; ++m1) (m1 < NB ? h0 : h1)[rb + L2 * (m1 % NB) + m2] = v[m1];
+          for (int m1 = 0; m1 < NOUT; ++m1) hp[m1 / NB][rb + L2 * (m1 % NB) + m2] = v[m1];
         }
       }
       __syncwarp();
     }
-    if constexpr (CL == 2) cooperative_groups::this_cluster().sync();  // both halves written
+    if constexpr (CL > 1) cooperative_groups::this_cluster().sync();  // every part written
     else __syncthreads();
   } else {
     for (int r0 = 0; r0 <= N; r0 += Q) {
@@ -630,7 +706,7 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
         const C* in = X + (((long long)p * (N + 1) + (r0 + r)) * G + z) * L + k1;
         C v[L2];
 #pragma unroll
-        for (int k2 = 0; k2 < L2; ++k2) v[k2] = in[L1 * k2];
+        for (int k2 = 0; k2 < L2; ++k2) v[k2] = ldx<COH>(in + L1 * k2);
         dft<L2, 1, 1>(v);
         C* q = S + r * Scr<L1, L2>::line + k1;
         q[0] = v[0];
@@ -652,11 +728,13 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
       __syncthreads();
     }
   }
-  // fold the half spectrum into Z (units (y, k), k = 0..n/2, y fastest)
+  // fold the half spectrum into Z (units (y, k), k = 0..n/2, y fastest);
+  // Q = 0: row 0 holds the lines of rows 0 and n as (real, imaginary) parts
+  constexpr bool MERGE = Q == 0;
   for (int u = tid; u < NY * (N / 2 + 1); u += NT) {
     const int k = u / NY, y = u - k * NY;
     if (k == 0) {
-      const R x0 = Sl[y].x, xn = Sl[srow<SP, X1>(N) + y].x;
+      const R x0 = Sl[y].x, xn = MERGE ? Sl[y].y : Sl[srow<SP, X1>(N) + y].x;
       Sl[y] = mkc<C>(x0 + xn, x0 - xn);
     } else if (2 * k == N) {
       C* rk = Sl + srow<SP, X1>(k) + y;
@@ -705,6 +783,12 @@ k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __rest
   }
 }
 
+template <typename R, int N, int NT, int MINB, int Q, int CL, bool PER>
+__global__ void __launch_bounds__(NT, MINB)
+k_inv_yx(const cplx<R>* __restrict__ X, R* __restrict__ V, const cplx<R>* __restrict__ tw_g) {
+  inv_yx_unit<R, N, NT, Q, CL, PER, false>(X, V, tw_g, blockIdx.x, blockIdx.y);
+}
+
 // ------------------------------------------------------------------- accum
 // One pair tile: orbitals i0..i0+ti-1 (block I) and j0..j0+tj-1 (block J);
 // off-diagonal tiles hold all ti*tj pairs (slot a*tj + b), diagonal tiles
@@ -718,24 +802,24 @@ template <> struct vecty<float, 1> { using type = float; };
 template <> struct vecty<double, 2> { using type = double2; };
 template <> struct vecty<double, 1> { using type = double; };
 
-template <typename R, int VEC>
+template <typename R, int VEC, bool COH = false>
 __device__ __forceinline__ void vload(const R* p, R (&v)[VEC]) {
   if constexpr (VEC == 1) {
-    v[0] = *p;
+    v[0] = ldx<COH>(p);
   } else {
     using V = typename vecty<R, VEC>::type;
-    const V t = *reinterpret_cast<const V*>(p);
+    const V t = ldx<COH>(reinterpret_cast<const V*>(p));
     const R* q = reinterpret_cast<const R*>(&t);
 #pragma unroll
     for (int e = 0; e < VEC; ++e) v[e] = q[e];
   }
 }
 // vx[0..VEC) += c * a  (FP64)
-template <typename R, int VEC>
+template <typename R, int VEC, bool COH = false>
 __device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
   if constexpr (VEC == 4) {
     double2* q = reinterpret_cast<double2*>(p);
-    double2 u = q[0], w = q[1];
+    double2 u = ldx<COH>(q), w = ldx<COH>(q + 1);
     u.x += c * (double)a[0];
     u.y += c * (double)a[1];
     w.x += c * (double)a[2];
@@ -744,12 +828,12 @@ __device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
     q[1] = w;
   } else if constexpr (VEC == 2) {
     double2* q = reinterpret_cast<double2*>(p);
-    double2 u = q[0];
+    double2 u = ldx<COH>(q);
     u.x += c * (double)a[0];
     u.y += c * (double)a[1];
     q[0] = u;
   } else {
-    p[0] += c * (double)a[0];
+    p[0] = ldx<COH>(p) + c * (double)a[0];
   }
 }
 
@@ -762,7 +846,7 @@ __device__ __forceinline__ void vacc(double* p, double c, const R (&a)[VEC]) {
 // gs = 0: the exchange action, vx_k += c * sum; gs > 0: the gradient of E_x,
 // vx_k += c gs f_k * sum (gs = 2 h^3: dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k,
 // Eq. daction), the per-orbital factor folded into the FP64 accumulation.
-template <typename R, int TM, int VEC, int MODE>
+template <typename R, int TM, int VEC, int MODE, bool COH = false>
 __device__ __forceinline__ void accum_tile(const R* __restrict__ psi, const R* __restrict__ V,
                                            double* __restrict__ vx,
                                            const double* __restrict__ occ, int i0, int ti_,
@@ -798,7 +882,7 @@ __device__ __forceinline__ void accum_tile(const R* __restrict__ psi, const R* _
       if (a >= ti || (diag && a > b)) continue;
       const int slot = diag ? a * tj - (a * (a - 1)) / 2 + (b - a) : a * tj + b;
       R v[VEC];
-      vload<R, VEC>(V + (long long)slot * n3 + r, v);
+      vload<R, VEC, COH>(V + (long long)slot * n3 + r, v);
 #pragma unroll
       for (int e = 0; e < VEC; ++e) {
         ai[a][e] += fb * v[e] * pb[e];
@@ -811,14 +895,14 @@ __device__ __forceinline__ void accum_tile(const R* __restrict__ psi, const R* _
       for (int e = 0; e < VEC; ++e) ai[b][e] += aj[e];
     } else {
       const double cb = gs != 0.0 ? c * (gs * occ[j0 + b]) : c;
-      vacc<R, VEC>(vx + (long long)(j0 + b) * n3 + r, cb, aj);
+      vacc<R, VEC, COH>(vx + (long long)(j0 + b) * n3 + r, cb, aj);
     }
   }
 #pragma unroll
   for (int a = 0; a < TM; ++a)
     if (a < ti) {
       const double ca = gs != 0.0 ? c * (gs * occ[i0 + a]) : c;
-      vacc<R, VEC>(vx + (long long)(i0 + a) * n3 + r, ca, ai[a]);
+      vacc<R, VEC, COH>(vx + (long long)(i0 + a) * n3 + r, ca, ai[a]);
     }
 }
 
@@ -845,13 +929,16 @@ struct TileDesc {
 
 // One tile per blockIdx.y; full tiles take the specialised bodies (the branch
 // is uniform over a block).  grad != 0: gradient of E_x (see accum_tile).
-template <typename R, int TM, int VEC>
-__global__ void __launch_bounds__(256, 2)
-k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
-              double* const* __restrict__ vx_tab, const double* __restrict__ occ,
-              const TileDesc* __restrict__ tiles, int grad, long long n3) {
-  const TileDesc t = tiles[blockIdx.y];
-  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * VEC;
+template <typename R, int TM, int VEC, bool COH>
+__device__ __forceinline__ void accum_batch_unit(const R* const* __restrict__ psi_tab,
+                                                 const R* __restrict__ V,
+                                                 double* const* __restrict__ vx_tab,
+                                                 const double* __restrict__ occ,
+                                                 const TileDesc* __restrict__ tiles, int grad,
+                                                 long long n3, const int bx, const int by,
+                                                 const int nt) {
+  const TileDesc t = tiles[by];
+  const long long r = (bx * (long long)nt + threadIdx.x) * VEC;
   if (r >= n3) return;
   const R* __restrict__ psi = psi_tab[t.mol];
   double* __restrict__ vx = vx_tab[t.mol];
@@ -860,12 +947,21 @@ k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
   const double gs = grad ? t.g2h3 : 0.0;
   if (t.ti == TM && t.tj == TM) {
     if (t.diag)
-      accum_tile<R, TM, VEC, 2>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 1, t.c, gs, n3, r);
+      accum_tile<R, TM, VEC, 2, COH>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 1, t.c, gs, n3, r);
     else
-      accum_tile<R, TM, VEC, 1>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 0, t.c, gs, n3, r);
+      accum_tile<R, TM, VEC, 1, COH>(psi, Vt, vx, oc, t.i0, TM, t.j0, TM, 0, t.c, gs, n3, r);
   } else {
-    accum_tile<R, TM, VEC, 0>(psi, Vt, vx, oc, t.i0, t.ti, t.j0, t.tj, t.diag, t.c, gs, n3, r);
+    accum_tile<R, TM, VEC, 0, COH>(psi, Vt, vx, oc, t.i0, t.ti, t.j0, t.tj, t.diag, t.c, gs, n3, r);
   }
+}
+
+template <typename R, int TM, int VEC>
+__global__ void __launch_bounds__(256, 2)
+k_accum_batch(const R* const* __restrict__ psi_tab, const R* __restrict__ V,
+              double* const* __restrict__ vx_tab, const double* __restrict__ occ,
+              const TileDesc* __restrict__ tiles, int grad, long long n3) {
+  accum_batch_unit<R, TM, VEC, false>(psi_tab, V, vx_tab, occ, tiles, grad, n3, blockIdx.x,
+                                      blockIdx.y, blockDim.x);
 }
 
 }  // namespace exx

@@ -11,6 +11,7 @@
 
 #include "exx_gain.cuh"
 #include "exx_kernels.cuh"
+#include "exx_persist.cuh"
 
 namespace exx {
 
@@ -30,7 +31,7 @@ struct Ops {
   // gy[2n], gz[2nz]
   void (*gains)(double* gx, double* gy, double* gz) = nullptr;
   bool table_fold_y = false;  // kernel-table layout (build_kernel_table)
-  bool clustered = false;     // slab kernels launched as two-CTA clusters
+  bool clustered = false;     // slab kernels launched as CTA clusters
   // psi_tab (device array of orbital-array pointers, indexed by the pair's
   // molecule slot) may be null, in which case every pair reads psi
   void (*fwd_xy)(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
@@ -42,6 +43,11 @@ struct Ops {
                 int* err, int npair, bool energy_only, cudaStream_t st) = nullptr;
   bool stage_table = false;
   void (*inv_yx)(const void* X3, void* V, const void* tw, int npair, cudaStream_t st) = nullptr;
+  // persistent batched kernel (FP32, free boundary conditions, slab kernels
+  // without clusters): threads per CTA, and the launch of a queue
+  bool persist_ok = false;
+  int persist_nt = 0;
+  cudaError_t (*persist)(const PersistArgs& a, cudaStream_t st) = nullptr;
 };
 
 constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation of one CTA
@@ -53,9 +59,11 @@ constexpr size_t kSmemPerCTA = 227 * 1024 - 256;  // largest dynamic allocation 
 //   (small slabs: periodic 96^3 -6.6% per exx_apply against two CTAs of 320
 //   with 160 threads per CTA, a further -1.8% with 192),
 //   two CTAs of 320 when they fit in half an SM, else one CTA of 640;
-//   the same with the slab split over a two-CTA cluster (cl = 2, half the
-//   columns per CTA; fixed2 is its fixed part), when allowed, with 640 or
-//   else 320 threads per CTA;
+//   FP32: the slab split over a four-CTA cluster (cl = 4, a quarter of the
+//   columns per CTA; fixed4 is its fixed part) as two CTAs of 320 per SM;
+//   the slab split over a two-CTA cluster (cl = 2, half the columns per CTA;
+//   fixed2 is its fixed part), when allowed, with 640 or else 320 threads per
+//   CTA; over a four-CTA cluster with 320 threads (FP64 n = 160);
 //   CTA-wide batches of q rows.
 // Measured at n = 96 (64 orbitals): warp-owned y passes with two CTAs per SM
 // take fwd_xy from 13.3 to 13.0 ms and inv_yx from 13.5 to 11.1 ms per
@@ -66,7 +74,8 @@ struct SlabShape {
   bool fits;
 };
 constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_t line,
-                               bool prefer_two, bool fp32) {
+                               bool prefer_two, bool fp32, size_t fixed4 = 0,
+                               bool split4_ok = false) {
   const size_t half = 113 * 1024;
   if (prefer_two && fp32 && fixed + 12 * line <= 56 * 1024)  // small slabs: four CTAs of 192
     return SlabShape{0, 192, 4, 1, fixed + 12 * line, true};
@@ -74,10 +83,17 @@ constexpr SlabShape slab_shape(size_t fixed, size_t fixed2, bool split_ok, size_
     return SlabShape{0, 160, 4, 1, fixed + 10 * line, true};
   if (prefer_two && fixed + 20 * line <= half) return SlabShape{0, 320, 2, 1, fixed + 20 * line, true};
   if (fixed + 40 * line <= kSmemPerCTA) return SlabShape{0, 640, 1, 1, fixed + 40 * line, true};
+  // FP32 slabs beyond one SM (n = 160): four-CTA clusters of 320 threads, two
+  // CTAs per SM, so that one CTA's transform phases overlap the other's memory
+  // phases (a two-CTA cluster of 640 threads holds a whole SM)
+  if (fp32 && split4_ok && fixed4 + 20 * line <= half)
+    return SlabShape{0, 320, 2, 4, fixed4 + 20 * line, true};
   if (split_ok && fixed2 + 40 * line <= kSmemPerCTA)
     return SlabShape{0, 640, 1, 2, fixed2 + 40 * line, true};
   if (split_ok && fixed2 + 20 * line <= kSmemPerCTA)  // e.g. FP64 n = 128
     return SlabShape{0, 320, 1, 2, fixed2 + 20 * line, true};
+  if (split4_ok && fixed4 + 20 * line <= kSmemPerCTA)  // FP64 n = 160
+    return SlabShape{0, 320, 1, 4, fixed4 + 20 * line, true};
   if (prefer_two && fixed + 8 * line <= half) {
     size_t q = (half - fixed) / line;
     q = q > 32 ? 32 : q;
@@ -220,13 +236,18 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   // on a whole number of length-L2 groups)
   static constexpr bool split_ok = X1 && L1 && G % 2 == 0 && (G / 2) % L2 == 0;
   static constexpr size_t slab2 = split_ok ? (size_t)slab_elems(N, G / 2) * sizeof(C) : 0;
+  // four-CTA split: a quarter of the columns per CTA
+  static constexpr bool split4_ok = X1 && L1 && G % 4 == 0 && (G / 4) % L2 == 0;
+  static constexpr size_t slab4 = split4_ok ? (size_t)slab_elems(N, G / 4) * sizeof(C) : 0;
   static constexpr size_t line = (size_t)((L2 * (L1 + 1)) | 1) * sizeof(C);
   static constexpr SlabShape SA = slab_shape(slab + (size_t)(L + N) * sizeof(C),
                                              slab2 + (size_t)(L + N) * sizeof(C), split_ok, line,
-                                             true, sizeof(R) == 4);
+                                             true, sizeof(R) == 4,
+                                             slab4 + (size_t)(L + N) * sizeof(C), split4_ok);
   static constexpr SlabShape SC = slab_shape(slab + (size_t)2 * L * sizeof(C),
                                              slab2 + (size_t)2 * L * sizeof(C), split_ok, line,
-                                             true, sizeof(R) == 4);
+                                             true, sizeof(R) == 4,
+                                             slab4 + (size_t)2 * L * sizeof(C), split4_ok);
   static constexpr int QA = SA.q, NT_A = SA.nt, MINB_A = SA.minb, CL_A = SA.cl;
   static constexpr int QC = SC.q, NT_C = SC.nt, MINB_C = SC.minb, CL_C = SC.cl;
   static constexpr size_t smem_a = SA.smem, smem_c = SC.smem;
@@ -238,6 +259,9 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   // 192-point lines: eight warps with the kernel table read from L2, four
   // CTAs per SM, -2.3% zconv at 96^3 against twelve warps with the staged
   // table at three CTAs)
+  // (FP32 L2 = 20, 320-point lines of free 160^3: ten warps, two CTAs per SM;
+  // 16 columns per CTA with two units per warp, five warps and four CTAs per
+  // SM, measured 7% slower)
   static constexpr int NW = (sizeof(R) == 4 && LZ2 == 6)    ? 6
                             : (sizeof(R) == 4 && LZ2 == 14) ? 8
                             : (sizeof(R) == 4 && LZ2 == 12) ? 8
@@ -257,12 +281,41 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   // CTAs per SM the zconv register budget is sized for (FP32): as many as
   // shared memory allows, at least three and at most eight; else two
   static constexpr int CTAS_B = (int)((228 * 1024) / (smem_b + 1024));
-  static constexpr int MINB_B = (sizeof(R) == 4 && CTAS_B >= 3) ? (CTAS_B < 8 ? CTAS_B : 8) : 2;
+  static constexpr int MINB_B = (sizeof(R) == 4 && CTAS_B >= 3) ? (CTAS_B < 8 ? CTAS_B : 8)
+                                : CTAS_B >= 2 ? 2 : 1;
   // ky-folded kernel table where the unfolded one would exceed 24 MB
   static constexpr bool fold_y = !mixed && !stage_g && (size_t)(N + 1) * (2 * N) * (2 * N) * sizeof(R) > (24u << 20);
   static constexpr bool ok = L1 != 0 && LZ1 != 0 && X1 != 0 && SA.fits && SC.fits && smem_b <= kSmemPerCTA;
   template <bool EO> static constexpr auto zk() {
     return &k_zconv<R, N, NW, MINB_B, stage_g, fold_y, PER, EO, NZ, PERZ>;
+  }
+  // persistent batched kernel: the slab kernels' CTA shape (one per SM share),
+  // shared memory for the largest pass
+  static constexpr bool persist_ok = sizeof(R) == 4 && !PER && !mixed && ok && QA == 0 &&
+                                     QC == 0 && CL_A == 1 && CL_C == 1 && NT_A == NT_C;
+  static constexpr int NT_P = NT_A;
+  static constexpr int MINB_P = MINB_A < MINB_C ? MINB_A : MINB_C;
+  static constexpr size_t smem_p = smem_a > smem_c ? (smem_a > smem_b0 ? smem_a : smem_b0)
+                                                   : (smem_c > smem_b0 ? smem_c : smem_b0);
+  static constexpr auto pk() { return &k_persist<N, NT_P, MINB_P, fold_y>; }
+  static cudaError_t persist(const PersistArgs& a, cudaStream_t st) {
+    if constexpr (persist_ok) {
+      static int grid = 0;  // resident CTAs on this device
+      if (grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(pk(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pk(), NT_P, smem_p);
+        if (e != cudaSuccess) return e;
+        grid = (per > 0 ? per : 1) * sms;
+      }
+      if (a.total <= 0) return cudaSuccess;  // set-up only (before any capture)
+      const int g = a.total < grid ? a.total : grid;
+      pk()<<<g > 0 ? g : 1, NT_P, smem_p, st>>>(a);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;
   }
 
   // gains of the x and y transforms, and of the z transform
@@ -294,7 +347,7 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   static void fwd_xy(const void* psi, const void* const* psi_tab, const int4* pairs, int npair,
                      void* X, const void* tw, long long n3, cudaStream_t st) {
     if constexpr (ok)
-      launch_slab<CL_A>(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A, PER>, dim3(G * CL_A, npair), NT_A,
+      launch_slab<CL_A>(k_fwd_xy<R, N, NT_A, MINB_A, QA, CL_A, PER>, dim3(CL_A * npair, G), NT_A,
                         smem_a, st, static_cast<const R*>(psi),
                         reinterpret_cast<const R* const*>(psi_tab), pairs, static_cast<C*>(X),
                         static_cast<const C*>(tw), n3);
@@ -302,7 +355,7 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   static void zconv(void* X, const void* Gs, const void* tw, const CUtensorMap* gmap,
                     double* epart, int* err, int npair, bool energy_only, cudaStream_t st) {
     if constexpr (ok) {
-      const dim3 grid(NYB, N + 1, npair);
+      const dim3 grid(npair, NYB, N + 1);
       CUtensorMap m{};
       if (stage_g && gmap) m = *gmap;
       if (energy_only)
@@ -342,6 +395,9 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
     o.fwd_xy = &fwd_xy;
     o.zconv = &zconv;
     o.inv_yx = &inv_yx;
+    o.persist_ok = persist_ok;
+    o.persist_nt = NT_P;
+    if constexpr (persist_ok) o.persist = &persist;
     return o;
   }
 };

@@ -71,6 +71,7 @@ EXPORTS = {
     "exx_batch_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "exx_batch_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "exx_batch_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "exx_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "exx_batch_pair_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _c_double_p,
                                                ctypes.c_void_p]),
     "exx_batch_info": (ctypes.c_int, [ctypes.c_void_p, _c_int_p, _c_int_p, _c_size_p, _c_int_p,
@@ -468,6 +469,12 @@ class ExxBatch:
         """Capture each call kind once into a CUDA graph and replay it (needs a
         created, non-default stream)."""
         _check(self.lib.exx_batch_graph(self.handle, int(bool(enable))), "exx_batch_graph")
+
+    def persistent(self, enable=True, stream=None):
+        """Run each (n, h) group as one launch of the persistent kernel over a
+        device work queue (exx_batch_set_persistent)."""
+        _check(self.lib.exx_batch_set_persistent(self.handle, int(bool(enable)), _stream_ptr(stream)),
+               "exx_batch_set_persistent")
 
     def pair_energies(self, mol, stream=None):
         """E_ij of molecule ``mol`` from the last call (as ExxPlan.pair_energies)."""

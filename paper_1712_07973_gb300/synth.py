@@ -122,8 +122,9 @@ def _make_orbitals_torch(r: OrbitalRecipe, dtype, device):
         yx_t = torch.from_numpy((gy[:, None, :] * gx[None, :, :]).reshape(n * n, G)).to(device)
         phi[o] = (gz_t @ yx_t.T).reshape(-1)
     S = (r.h ** 3) * (phi @ phi.T)
-    w, U = torch.linalg.eigh(S)
-    Sm12 = (U / torch.sqrt(w)) @ U.T
+    # the norb x norb eigenproblem on the host (NumPy, as in make_orbitals)
+    w, U = np.linalg.eigh(S.cpu().numpy())
+    Sm12 = torch.from_numpy((U / np.sqrt(w)) @ U.T).to(device)
     psi = (Sm12 @ phi).reshape(r.norb, n, n, n)
     tdt = {np.float64: torch.float64, np.float32: torch.float32}[np.dtype(dtype).type]
     return psi.to(tdt).contiguous()

@@ -13,7 +13,9 @@
   accumulation) equals 2 f_k h^3 times exx_apply's action.
 """
 
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -130,16 +132,33 @@ def test_fp32_gradient_matches_fp64_on_the_128_orbital_workload(env):
     occ = np.full(r.norb, r.occupation)
     p64 = exx.ExxPlan(r.n, r.h, r.alpha, occ, precision="fp64")
     E64, g64 = p64.gradient(psi64)
+    Eij64 = p64.pair_energies()
     p64.close()
     p32 = exx.ExxPlan(r.n, r.h, r.alpha, occ, precision="fp32")
     psi = psi64.float().requires_grad_(True)
     E32 = ag.exx_energy(psi, p32)
     E32.backward()
+    Eij32 = p32.pair_energies()
     p32.close()
     assert abs(float(E32.item()) - E64) <= 1e-6
     num = float(torch.linalg.vector_norm(psi.grad.double() - g64).item())
     den = float(torch.linalg.vector_norm(g64).item())
     assert num <= 1e-5 * den, num / den
+    # both against the stored oracle values of this workload (E_x, all 8,256
+    # E_ij, the action at 256 seeded points), written by tests/golden/make_golden.py
+    path = os.path.join(os.path.dirname(__file__), "golden", "c3_grad_n128_N128.json")
+    with open(path) as fh:
+        gold = json.load(fh)
+    assert abs(E64 - gold["E_x"]) <= 1e-10 * abs(gold["E_x"])
+    assert abs(float(E32.item()) - gold["E_x"]) <= 1e-6
+    Eo = np.asarray(gold["E_ij"])
+    assert np.max(np.abs(Eij64 - Eo)) <= 1e-10 * np.max(np.abs(Eo))
+    assert np.max(np.abs(Eij32 - Eo)) <= 1e-6
+    pts = np.asarray(gold["sample_points"])
+    vxo = np.asarray(gold["vx_samples"])
+    vx64 = (g64 / (2.0 * r.occupation * r.h ** 3)).cpu().numpy()
+    got = vx64[pts[:, 0], pts[:, 1], pts[:, 2], pts[:, 3]]
+    assert np.max(np.abs(got - vxo)) <= 1e-10 * np.max(np.abs(vxo))
 
 
 def test_autograd_workload_128_orbitals_n128_fd(env):

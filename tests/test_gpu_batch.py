@@ -233,3 +233,97 @@ def test_batch_two_lanes_equal_one_lane(env, monkeypatch):
     assert torch.equal(E1, E2)
     for a, c in zip(v1, v2):
         assert torch.equal(a, c)
+
+
+MANY = [  # (n, N, h, alpha): several waves per group (slot reuse, tile order)
+    (12, 20, 0.45, 0.25), (12, 13, 0.45, 0.25), (16, 17, 0.4, 0.25), (8, 5, 0.5, 0.3),
+    (10, 9, 0.5, 0.2),
+]
+
+
+@pytest.mark.parametrize("lanes", ["1", "2"])
+def test_persistent_queue_equals_launch_per_pass(env, monkeypatch, lanes):
+    # one persistent launch per (n, h) group over a device work queue against
+    # five launches per wave: the same per-CTA code and tile order, compiled
+    # into another kernel (the compiler may contract other multiply-adds, so
+    # equal to FP32 rounding: Vx psi to 1e-6 of its largest entry, E_ij to
+    # 1e-7 relative); each schedule bit-identical eagerly and through the
+    # captured graph, and both against the oracle
+    torch, dev, exx = env
+    monkeypatch.setenv("EXX_LANES", lanes)
+    psis, occs, mols = [], [], []
+    for k, (n, N, h, a) in enumerate(MANY):
+        psis.append(_mol(n, N, 400 + k, h))
+        occs.append(np.linspace(0.5, 2.0, N))
+        mols.append({"n": n, "h": h, "alpha": a, "occupations": occs[-1]})
+    pt = [torch.from_numpy(p).to(dev, torch.float32) for p in psis]
+    res = []
+    for persistent in (False, True):
+        b = exx.ExxBatch(mols)
+        b.persistent(persistent)
+        vx = [torch.empty_like(p) for p in pt]
+        b.set_buffers(pt, vx)
+        Ea = b.apply().cpu()
+        va = [v.clone() for v in vx]
+        Eij = [b.pair_energies(k) for k in range(len(mols))]
+        Eg = b.gradient().cpu()
+        vg = [v.clone() for v in vx]
+        Ee = b.energy().cpu()
+        b.graph(True)
+        s = torch.cuda.Stream()
+        E2 = torch.zeros(len(mols), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                b.apply(E2, stream=s)
+        s.synchronize()
+        assert torch.equal(E2.cpu(), Ea)
+        assert all(torch.equal(a, c) for a, c in zip(vx, va))
+        info = b.info()
+        b.close()
+        res.append((Ea, va, Eij, Eg, vg, Ee, info))
+    (Ea0, va0, Eij0, Eg0, vg0, Ee0, i0), (Ea1, va1, Eij1, Eg1, vg1, Ee1, i1) = res
+    assert i1["launches_apply"] == len({(m["n"], m["h"]) for m in mols}) + 2
+    assert torch.allclose(Ea1, Ea0, rtol=1e-7, atol=0)
+    assert torch.allclose(Eg1, Eg0, rtol=1e-7, atol=0)
+    assert torch.allclose(Ee1, Ee0, rtol=1e-7, atol=0)
+    for k in range(len(mols)):
+        for x1, x0 in ((va1[k], va0[k]), (vg1[k], vg0[k])):
+            assert torch.allclose(x1, x0, rtol=0, atol=1e-6 * float(x0.abs().max()))
+        assert np.allclose(Eij1[k], Eij0[k], rtol=1e-7, atol=0)
+    # and the oracle
+    for k, (m, p, occ) in enumerate(zip(mols, psis, occs)):
+        Gh = o.kernel_spectrum(o.kernel_real_space(m["n"], m["h"]))
+        Eo, vxo, _ = o.exx(p, occ, m["alpha"], m["h"], Gh)
+        assert abs(float(Ea1[k]) - Eo) <= 1e-6
+        assert np.max(np.abs(va1[k].double().cpu().numpy() - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+
+
+def test_persistent_queue_wait_times_out_and_context_survives(env, monkeypatch):
+    # a queue segment made to wait for one that never completes (host-side
+    # test hook): the bounded device-side wait runs out, the launch skips the
+    # rest and ends, the next synchronising call reports EXX_ERR_TIMEOUT, and
+    # the context still computes correct energies
+    torch, dev, exx = env
+    psis, occs, mols = _small(env)
+    pt = [torch.from_numpy(p).to(dev, torch.float32) for p in psis]
+    monkeypatch.setenv("EXX_TEST_STALL_QUEUE", "1")
+    b = exx.ExxBatch(mols)
+    b.persistent(True)
+    vx = [torch.empty_like(p) for p in pt]
+    b.set_buffers(pt, vx)
+    b.apply()
+    with pytest.raises(exx.ExxError) as ei:
+        b.pair_energies(0)
+    assert ei.value.status == 4
+    b.close()
+    monkeypatch.delenv("EXX_TEST_STALL_QUEUE")
+    b = exx.ExxBatch(mols)
+    b.persistent(True)
+    b.set_buffers(pt, vx)
+    E = b.apply().cpu()
+    for k, (m, p, occ) in enumerate(zip(mols, psis, occs)):
+        Gh = o.kernel_spectrum(o.kernel_real_space(m["n"], m["h"]))
+        Eo, vxo, _ = o.exx(p, occ, m["alpha"], m["h"], Gh)
+        assert abs(float(E[k]) - Eo) <= 1e-6
+        assert np.max(np.abs(vx[k].double().cpu().numpy() - vxo)) <= 2e-6 * np.max(np.abs(vxo))
+    b.close()

@@ -39,6 +39,26 @@ def test_fp32_large_grids_against_oracle(env, n, h):
     assert np.max(np.abs(vx.double().cpu().numpy() - vxo)) <= 2e-6 * np.max(np.abs(vxo))
 
 
+def test_fp64_160_four_cta_clusters_against_oracle(env):
+    # FP64 at 160^3 (320^3 padded): slab kernels as four-CTA clusters, the
+    # 320-point z lines in one CTA per SM; 1e-10 relative
+    torch, dev, exx = env
+    n, h = 160, 0.42
+    r = synth.OrbitalRecipe(n=n, h=h, norb=2, nsites=3, seed=660, gauss_per_orb=6,
+                            sigma=(0.7, 1.8), p_type=True)
+    psi = synth.make_orbitals(r)
+    occ = np.array([2.0, 1.0])
+    plan = exx.ExxPlan(n, h, 0.25, occ, precision="fp64")
+    E, vx = plan.apply(torch.from_numpy(psi).to(dev))
+    Eij = plan.pair_energies()
+    plan.close()
+    Gh = o.kernel_spectrum(o.kernel_real_space(n, h))
+    Eo, vxo, Eijo = o.exx(psi, occ, 0.25, h, Gh)
+    assert abs(E - Eo) <= 1e-10 * abs(Eo)
+    assert np.max(np.abs(Eij - Eijo[np.triu_indices(2)])) <= 1e-10 * np.max(np.abs(Eijo))
+    assert np.max(np.abs(vx.cpu().numpy() - vxo)) <= 1e-10 * np.max(np.abs(vxo))
+
+
 @pytest.mark.slow
 def test_large_cluster_512_orbitals_n160(env):
     # 512 orbitals on 160^3 (320^3 padded), h = 0.42, 256 sites on a jittered

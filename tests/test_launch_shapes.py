@@ -75,9 +75,7 @@ def shapes(tmp_path_factory):
 
 def test_every_registered_configuration_is_supported(shapes):
     bad = [(s["bc"], s["n"], s["prec"]) for s in shapes if not s["ok"]]
-    # FP64 at the largest free and periodic sizes exceeds one SM's shared memory
-    # (plan creation returns EXX_ERR_NOT_SUPPORTED there)
-    assert sorted(bad) == [("free", 160, "fp64")], bad
+    assert bad == [], bad
     assert len([s for s in shapes if s["prec"] == "fp32" and s["ok"]]) == len(shapes) // 2
 
 
@@ -103,3 +101,18 @@ def test_bench_workload_shapes(shapes):
     assert (s["nt_a"], s["minb_a"], s["cl_a"]) == (320, 2, 1)
     assert (s["nt_c"], s["minb_c"], s["cl_c"]) == (320, 2, 1)
     assert (s["nw"], s["minb_b"], s["stage"]) == (8, 4, 0)
+
+
+def test_largest_grid_shapes(shapes):
+    # n = 160: the slab kernels run as four-CTA clusters, two CTAs of 320
+    # threads per SM in FP32 and one in FP64 (whose slab quarter and scratch
+    # take most of an SM)
+    f32 = next(s for s in shapes if s["bc"] == "free" and s["n"] == 160 and s["prec"] == "fp32")
+    f64 = next(s for s in shapes if s["bc"] == "free" and s["n"] == 160 and s["prec"] == "fp64")
+    assert (f32["nt_a"], f32["minb_a"], f32["cl_a"]) == (320, 2, 4)
+    assert (f32["nt_c"], f32["minb_c"], f32["cl_c"]) == (320, 2, 4)
+    assert (f64["nt_a"], f64["minb_a"], f64["cl_a"]) == (320, 1, 4)
+    assert (f64["nt_c"], f64["minb_c"], f64["cl_c"]) == (320, 1, 4)
+    assert f64["minb_b"] == 1
+    # FP32 zconv on 320-point lines: 32 columns, ten warps, two CTAs per SM
+    assert (f32["w"], f32["nw"], f32["minb_b"]) == (32, 10, 2)
