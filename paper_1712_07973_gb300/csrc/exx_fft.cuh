@@ -313,5 +313,13 @@ __host__ __device__ constexpr int split_l1(int L) {
     if (L % a == 0 && L / a <= 20 && smooth7(a) && smooth7(L / a)) return a;
   return 0;
 }
+// Split of the z lines (zconv).  Its middle pass, the heaviest (forward DFT
+// of length L2, kernel multiply, inverse), has L1 units over the CTA's warps:
+// where L = 20 L2 with 12 <= L2 <= 16 (L = 320), L1 = 20 and L2 = 16 give ten
+// warps two full rounds there, against 16 units of DFT20 for the 16 x 20
+// split (six of ten warps busy in the second round).
+__host__ __device__ constexpr int split_z(int L) {
+  return (L % 20 == 0 && L / 20 >= 12 && L / 20 <= 16 && smooth7(L / 20)) ? 20 : split_l1(L);
+}
 
 }  // namespace exx

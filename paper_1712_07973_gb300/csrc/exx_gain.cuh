@@ -45,10 +45,12 @@ template <> struct creal<F32c2> { using type = F32c; };
 // PER: periodic boundary conditions (full lines of 2N points, nothing pruned);
 // otherwise free (lines of N points padded to 2N).  S: the model's scalar
 // (F32c; a type with the same interface that does not round gives |d|^2 = 1).
-template <int N, bool PER = false, typename S = F32c> struct GainModel {
+// L1O: the line split of the modelled pass (0: split_l1, the y pass; the z
+// pass of zconv uses split_z).
+template <int N, bool PER = false, typename S = F32c, int L1O = 0> struct GainModel {
   using R = S;
   using C = typename cvec<S>::type;
-  static constexpr int L = 2 * N, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
+  static constexpr int L = 2 * N, L1 = L1O ? L1O : split_l1(L), L2 = L / L1, H1 = L1 / 2;
   static constexpr int X1 = split_x(N), X2 = N / X1;
   static constexpr int G = PER ? L : N;  // input samples per line
   static constexpr int NIN = PER ? L1 : H1;

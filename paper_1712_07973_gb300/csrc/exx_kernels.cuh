@@ -444,7 +444,7 @@ __device__ __forceinline__ void zconv_unit(cplx<R>* __restrict__ X, const R* __r
                                            const int p) {
   using C = cplx<R>;
   constexpr int LY = 2 * N;  // ky extent: the row stride of X and of the kernel table
-  constexpr int L = 2 * NZ, L1 = split_l1(L), L2 = L / L1, H1 = L1 / 2;
+  constexpr int L = 2 * NZ, L1 = split_z(L), L2 = L / L1, H1 = L1 / 2;
   constexpr int W = LY < 32 ? LY : 32;
   constexpr int M = N + 1;
   static_assert((PER ? 2 * N : N) == (PERZ ? 2 * NZ : NZ), "one grid size on all axes");
@@ -586,10 +586,12 @@ template <typename R, int N, int NW, int MINB, bool STAGE, bool FOLDY, bool PER,
 __global__ void __launch_bounds__(32 * NW, MINB)
 k_zconv(cplx<R>* __restrict__ X, const R* __restrict__ Gs, const cplx<R>* __restrict__ tw_g,
         double* __restrict__ epart, const __grid_constant__ CUtensorMap gmap, int* __restrict__ err) {
-  // grid (pairs, column blocks, kx): consecutive CTAs read the same kernel-table
-  // slice, which then comes from L2 for all pairs of the tile
+  // grid (column blocks, pairs, kx): consecutive CTAs read adjacent columns of
+  // the same rows of one pair's spectrum, and the CTAs of one kx plane for all
+  // pairs of the tile run together, so the plane's kernel-table rows come from
+  // L2 for every pair
   zconv_unit<R, N, NW, MINB, STAGE, FOLDY, PER, ENERGY_ONLY, NZ, PERZ, false>(
-      X, Gs, tw_g, epart, &gmap, err, blockIdx.y, blockIdx.z, blockIdx.x);
+      X, Gs, tw_g, epart, &gmap, err, blockIdx.x, blockIdx.z, blockIdx.y);
 }
 
 // ------------------------------------------------------------------ inv_yx

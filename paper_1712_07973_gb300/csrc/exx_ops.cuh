@@ -228,7 +228,7 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   static constexpr int L1 = split_l1(L);
   static constexpr int L2 = L1 ? L / L1 : 1;
   static constexpr int LZ = 2 * NZ;
-  static constexpr int LZ1 = split_l1(LZ);
+  static constexpr int LZ1 = split_z(LZ);
   static constexpr int LZ2 = LZ1 ? LZ / LZ1 : 1;
   static constexpr int X1 = split_x(N);
   static constexpr size_t slab = X1 ? (size_t)slab_elems(N, G) * sizeof(C) : 0;
@@ -259,10 +259,11 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   // 192-point lines: eight warps with the kernel table read from L2, four
   // CTAs per SM, -2.3% zconv at 96^3 against twelve warps with the staged
   // table at three CTAs)
-  // (FP32 L2 = 20, 320-point lines of free 160^3: ten warps, two CTAs per SM;
-  // 16 columns per CTA with two units per warp, five warps and four CTAs per
-  // SM, measured 7% slower)
-  static constexpr int NW = (sizeof(R) == 4 && LZ2 == 6)    ? 6
+  // (FP32 320-point lines of free 160^3, split 20 x 16 (split_z): ten warps, two
+  // CTAs per SM; 16 columns per CTA with two units per warp, five warps and
+  // four CTAs per SM, measured 7% slower)
+  static constexpr int NW = (sizeof(R) == 4 && LZ1 == 20)   ? 10  // 320-point lines (split_z)
+                            : (sizeof(R) == 4 && LZ2 == 6)  ? 6
                             : (sizeof(R) == 4 && LZ2 == 14) ? 8
                             : (sizeof(R) == 4 && LZ2 == 12) ? 8
                                                             : zconv_warps(LZ2);
@@ -321,11 +322,11 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   // gains of the x and y transforms, and of the z transform
   static void gains(double* gx, double* gy, double* gz) {
     GainModel<N, PER>::gains(gx, gy);
-    if constexpr (!mixed) {
+    if constexpr (!mixed && LZ1 == L1) {
       for (int k = 0; k < L; ++k) gz[k] = gy[k];
-    } else {
+    } else {  // the z line differs from the y line in length, periodicity or split
       double tx[NZ + 1];
-      GainModel<NZ, PERZ>::gains(tx, gz);
+      GainModel<NZ, PERZ, F32c, LZ1>::gains(tx, gz);
     }
   }
 
@@ -355,7 +356,7 @@ template <typename R, int N, bool PER = false, int NZ = N, bool PERZ = PER> stru
   static void zconv(void* X, const void* Gs, const void* tw, const CUtensorMap* gmap,
                     double* epart, int* err, int npair, bool energy_only, cudaStream_t st) {
     if constexpr (ok) {
-      const dim3 grid(npair, NYB, N + 1);
+      const dim3 grid(NYB, npair, N + 1);
       CUtensorMap m{};
       if (stage_g && gmap) m = *gmap;
       if (energy_only)

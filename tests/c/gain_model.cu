@@ -35,8 +35,8 @@ using namespace exx;
 
 // max deviation of the y/z line transform and of the x (real) transform from
 // the exact DFT of length 2N over every unit impulse within the inputs
-template <int N, bool PER, typename S> double transform_error() {
-  using M = GainModel<N, PER, S>;
+template <int N, bool PER, typename S, int L1O = 0> double transform_error() {
+  using M = GainModel<N, PER, S, L1O>;
   using C = typename M::C;
   constexpr int L = M::L, G = M::G;
   double err = 0.0;
@@ -59,20 +59,22 @@ template <int N, bool PER, typename S> double transform_error() {
   return err;
 }
 
-template <int N, bool PER, typename S> double gain_deviation() {
+template <int N, bool PER, typename S, int L1O = 0> double gain_deviation() {
   std::vector<double> gx(N + 1), gz(2 * N);
-  GainModel<N, PER, S>::gains(gx.data(), gz.data());
+  GainModel<N, PER, S, L1O>::gains(gx.data(), gz.data());
   double d = 0.0;
   for (double g : gx) d = std::fmax(d, std::fabs(g - 1.0));
   for (double g : gz) d = std::fmax(d, std::fabs(g - 1.0));
   return d;
 }
 
-template <int N, bool PER> void report() {
-  std::printf("{\"N\": %d, \"periodic\": %d, \"err32\": %.3e, \"err64\": %.3e, \"gdev32\": %.3e, "
-              "\"gdev64\": %.3e}\n",
-              N, (int)PER, transform_error<N, PER, F32c>(), transform_error<N, PER, F64x>(),
-              gain_deviation<N, PER, F32c>(), gain_deviation<N, PER, F64x>());
+// L1O: the line split of the modelled pass (0: the y pass; split_z(2N): zconv)
+template <int N, bool PER, int L1O = 0> void report() {
+  std::printf("{\"N\": %d, \"periodic\": %d, \"L1\": %d, \"err32\": %.3e, \"err64\": %.3e, "
+              "\"gdev32\": %.3e, \"gdev64\": %.3e}\n",
+              N, (int)PER, GainModel<N, PER, F32c, L1O>::L1, transform_error<N, PER, F32c, L1O>(),
+              transform_error<N, PER, F64x, L1O>(), gain_deviation<N, PER, F32c, L1O>(),
+              gain_deviation<N, PER, F64x, L1O>());
 }
 
 int main() {
@@ -80,6 +82,8 @@ int main() {
   report<12, false>();
   report<48, false>();
   report<96, false>();
+  report<160, false>();
+  report<160, false, split_z(320)>();  // zconv's 20 x 16 split of 320-point lines
   report<4, true>();
   report<24, true>();
   report<48, true>();

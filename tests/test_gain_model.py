@@ -30,6 +30,11 @@ def rows(tmp_path_factory):
     return [json.loads(ln) for ln in out.splitlines()]
 
 
+def test_both_splits_of_320_point_lines_are_modelled(rows):
+    # y pass 16 x 20, zconv 20 x 16 (split_z)
+    assert sorted(r["L1"] for r in rows if r["N"] == 160) == [16, 20]
+
+
 def test_model_with_exact_constants_is_the_dft(rows):
     for r in rows:
         assert r["err64"] <= 1e-12, r
