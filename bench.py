@@ -395,7 +395,8 @@ def fp32_vs_fp64_record(torch, dev, exx, synth, stream, ag):
     p64.close()
     rel = float(torch.linalg.vector_norm(g32 - g64).item() / torch.linalg.vector_norm(g64).item())
     rec = {"workload": f"{name}: 128 orbitals on 128^3 (256^3 padded), h = 0.37 -- the largest "
-                       "workload whose FP64 step fits the bench run (FP64 at 160^3 is not built)",
+                       "workload whose FP64 step fits the bench run (an FP64 step of the 512-orbital "
+                       "160^3 workload takes minutes)",
            "pairs": P, "what": "ms per E_x + gradient: ExxEnergy forward + backward (torch.autograd)",
            "fp32_ms_per_step": ms32, "fp64_plain_ms_per_step": ms64,
            "fp32_speedup_vs_fp64_plain": ms64 / ms32,
