@@ -231,7 +231,7 @@ exx_status_t exx_gradient_host(exx_plan_t plan, const void* psi_host, void* grad
 /*
  * exx_plan_set_lanes -- number of pipeline lanes (1 to 3) of later calls.
  * A plan is created with two lanes, or one where its slab kernels run as
- * two-CTA clusters (FP32 n = 160, FP64 n >= 96), or EXX_LANES = 1, 2 or 3
+ * CTA clusters (FP32 n = 160, FP64 n >= 96), or EXX_LANES = 1, 2 or 3
  * from the environment at creation; never more than it has pair tiles; each beyond
  * the first with its own internal stream and spectrum and potential
  * workspaces.  Consecutive tiles go round-robin over the lanes, so the

@@ -560,8 +560,8 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   }
   EXX_ALLOC(p->E_dev, sizeof(double));
   EXX_ALLOC(p->d_err, 2 * sizeof(int));
-  // pipeline lanes: two by default, one where the slab kernels run as two-CTA
-  // clusters (512 orbitals on 160^3: 17.5 s per step with one lane, 18.2 s
+  // pipeline lanes: two by default, one where the slab kernels run as CTA
+  // clusters (512 orbitals on 160^3: 16.53 s per step with one lane, 16.59 s
   // with two); EXX_LANES=1..3 at plan creation chooses; never more than the
   // plan has tiles
   {

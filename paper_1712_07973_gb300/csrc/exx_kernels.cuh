@@ -46,7 +46,7 @@ __host__ __device__ constexpr int split_x(int n) {
 }
 
 // Slab of the slab kernels: rows r = 0..n (k_x) of SP = ny + 1 complex values
-// (columns y; ny = n, or n / 2 per CTA of a two-CTA cluster), row r starting
+// (columns y; ny = n, or n / CL per CTA of a CL-CTA cluster), row r starting
 // at srow(r) = r SP + r / X1.  The extra slot every X1 rows skews the rows
 // n2 X1 + k1 that the 16 lanes of an x-pass unit group touch (consecutive n2)
 // onto distinct banks: the bank of (row, y) is 2 (n2 (X1 SP + 1) + k1 SP + y)

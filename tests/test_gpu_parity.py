@@ -549,6 +549,11 @@ def test_host_buffer_entry_point_overlapped_copies(torch_dev, prec, vx_fp64, N):
         Eh = plan.apply_host(ph, vh)
         assert Eh == E
         assert torch.equal(vh, vx.cpu())
+    # the gradient through host buffers equals the device gradient bit for bit
+    Eg, g = plan.gradient(p)
+    vh.fill_(float("nan"))
+    assert plan.gradient_host(ph, vh) == Eg == E
+    assert torch.equal(vh, g.cpu())
     plan.close()
 
 
