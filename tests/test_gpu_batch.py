@@ -327,3 +327,40 @@ def test_persistent_queue_wait_times_out_and_context_survives(env, monkeypatch):
         assert abs(float(E[k]) - Eo) <= 1e-6
         assert np.max(np.abs(vx[k].double().cpu().numpy() - vxo)) <= 2e-6 * np.max(np.abs(vxo))
     b.close()
+
+
+def test_persistent_mixed_groups_and_single_pair(env):
+    # persistent schedule with a group that keeps the launch-per-pass schedule
+    # (160^3: clustered slab kernels) next to persistent groups, and a molecule
+    # of one orbital (one pair, one wave): equal to the launch-per-pass
+    # schedule to FP32 rounding, and to the oracle
+    torch, dev, exx = env
+    spec = [(160, 2, 0.42, 0.25), (12, 1, 0.45, 0.25), (12, 6, 0.45, 0.25), (16, 9, 0.4, 0.3)]
+    psis, occs, mols = [], [], []
+    for k, (n, N, h, a) in enumerate(spec):
+        r = synth.OrbitalRecipe(n=n, h=h, norb=N, nsites=3, seed=700 + k, gauss_per_orb=6,
+                                sigma=(0.7, 1.8), p_type=True)
+        psis.append(synth.make_orbitals(r))
+        occs.append(np.linspace(1.0, 2.0, N))
+        mols.append({"n": n, "h": h, "alpha": a, "occupations": occs[-1]})
+    pt = [torch.from_numpy(p).to(dev, torch.float32) for p in psis]
+    res = []
+    for persistent in (False, True):
+        b = exx.ExxBatch(mols)
+        b.persistent(persistent)
+        vx = [torch.empty_like(p) for p in pt]
+        b.set_buffers(pt, vx)
+        E = b.gradient().cpu()
+        res.append((E, [v.clone() for v in vx], b.info()))
+        b.close()
+    (E0, v0, i0), (E1, v1, i1) = res
+    # groups (160, 0.42): one wave of five launches; (12, 0.45) and (16, 0.4): one
+    # persistent launch each; E_x totals and output conversion: two
+    assert i1["launches_apply"] == 5 + 2 + 2
+    assert torch.allclose(E1, E0, rtol=1e-7, atol=0)
+    for k, (m, p, occ) in enumerate(zip(mols, psis, occs)):
+        assert torch.allclose(v1[k], v0[k], rtol=0, atol=1e-6 * float(v0[k].abs().max()))
+        Gh = o.kernel_spectrum(o.kernel_real_space(m["n"], m["h"]))
+        Eo, go = o.exx_energy_gradient(p, occ, m["alpha"], m["h"], Gh)
+        assert abs(float(E1[k]) - Eo) <= 1e-6
+        assert np.max(np.abs(v1[k].double().cpu().numpy() - go)) <= 2e-6 * np.max(np.abs(go))

@@ -339,11 +339,17 @@ def test_dist_sharded_apply_nccl_against_oracle(torch_dev):
     try:
         plan = exx.ExxPlan(n, h, 0.25, occ, precision="fp64")
         E, vx = xdist.sharded_apply(plan, torch.from_numpy(psi_np).to(dev))
+        Eg, g = xdist.sharded_apply(plan, torch.from_numpy(psi_np).to(dev), gradient=True)
         plan.close()
     finally:
         tdist.destroy_process_group()
     assert abs(E - Eo) <= 1e-10 * abs(Eo)
     assert np.max(np.abs(vx.cpu().numpy() - vxo)) <= 1e-10 * np.max(np.abs(vxo))
+    # the gradient path: dE_x/dpsi_k = 2 f_k h^3 (Vx psi)_k against the oracle's
+    Gh = o.kernel_spectrum(o.kernel_real_space(n, h))
+    Eog, go = o.exx_energy_gradient(psi_np, occ, 0.25, h, Gh)
+    assert abs(Eg - Eog) <= 1e-10 * abs(Eog)
+    assert np.max(np.abs(g.cpu().numpy() - go)) <= 1e-10 * np.max(np.abs(go))
 
 
 def test_screened_erfc_kernel(torch_dev):
