@@ -529,7 +529,7 @@ def run_reference(a):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps,
         "ms_per_step_is": f"measured: one step = {per_step} sampled pair solves",
         "ms_per_full_workload_extrapolated": 1e3 * P / value,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": a.workload, "norb": N, "n": r.n, "pairs": P,
                                         "pairs_per_step": per_step, "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(),
@@ -647,7 +647,7 @@ def run_ours(a):
         prof = None
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "strong" if tdist else "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": a.workload, "bc": a.bc, "norb": N, "n": n,
                        "fft_grid": [2 * hh for hh in half_lines(n, a.bc)], "h": r.h,
