@@ -39,6 +39,10 @@ namespace exx {
 // line of length n (even samples + i odd samples), n = LX1 * LX2.  LX1 is even
 // when n is even, so that the half of the input beyond the data is pruned.
 __host__ __device__ constexpr int split_x(int n) {
+  // n = 160: 10 x 16 rather than 8 x 20, so that the x passes of a quarter
+  // slab (40 columns per CTA of 320 threads) run 640 and 400 units, two rounds
+  // each, rather than 800 (three rounds) and 320 (fwd_xy -2%)
+  if (n == 160) return 10;
   for (int a = 2; a <= 16; a += 2)
     if (n % a == 0 && n / a <= 20 && smooth7(a) && smooth7(n / a)) return a;
   if (n % 2 == 1 && n <= 16 && smooth7(n)) return n;
