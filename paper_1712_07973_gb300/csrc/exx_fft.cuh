@@ -250,6 +250,43 @@ template <int P, int S, int SIGN, typename C> EXX_HD void dft_composite(C* v) {
   sfor<P>([&](auto I) { v[I * S] = t[I]; });
 }
 
+// Coprime split P = A * B (A the largest power of P's smallest prime factor;
+// B = 1 for a prime power) and modular inverses, for the prime-factor
+// (Good-Thomas) form below.
+__host__ __device__ constexpr int pfa_a(int p) {
+  int q = 2;
+  while (p % q != 0) ++q;
+  int a = 1;
+  while (p % q == 0) {
+    p /= q;
+    a *= q;
+  }
+  return a;
+}
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return 1;
+}
+
+// P = A * B with gcd(A, B) = 1, no twiddle factors (Good-Thomas): input
+// index n = (B n1 + A n2) mod P, output index k = (B b k1 + A a k2) mod P with
+// b = B^-1 mod A and a = A^-1 mod B; then omega_P^(n k) = omega_A^(n1 k1)
+// omega_B^(n2 k2), so X = DFT_B over n2 of DFT_A over n1.  Both index maps are
+// register renames; the twiddles of the Cooley-Tukey form (4(A-1)(B-1) real
+// operations) disappear.
+template <int P, int S, int SIGN, typename C> EXX_HD void dft_pfa(C* v) {
+  constexpr int A = pfa_a(P), B = P / A;
+  constexpr int bi = inv_mod(B % A, A), ai = inv_mod(A % B, B);
+  C t[P];
+  sfor<A>([&](auto N1) { sfor<B>([&](auto N2) { t[N1 * B + N2] = v[((B * N1 + A * N2) % P) * S]; }); });
+  sfor<B>([&](auto N2) { dft<A, B, SIGN>(t + N2); });       // over n1 (stride B)
+  sfor<A>([&](auto K1) { dft<B, 1, SIGN>(t + K1 * B); });   // over n2
+  sfor<A>([&](auto K1) {
+    sfor<B>([&](auto K2) { v[(((long)B * bi * K1 + (long)A * ai * K2) % P) * S] = t[K1 * B + K2]; });
+  });
+}
+
 template <int P, int S, int SIGN, typename C> EXX_HD void dft(C* v) {
   if constexpr (P == 1) {
   } else if constexpr (P == 2) {
@@ -262,7 +299,8 @@ template <int P, int S, int SIGN, typename C> EXX_HD void dft(C* v) {
     dft_prime<P, S, SIGN>(v);
   } else {
     static_assert(first_factor<P>::value != P, "DFT length with a prime factor > 7");
-    dft_composite<P, S, SIGN>(v);
+    if constexpr (pfa_a(P) != P) dft_pfa<P, S, SIGN>(v);  // coprime factors
+    else dft_composite<P, S, SIGN>(v);                     // a prime power
   }
 }
 

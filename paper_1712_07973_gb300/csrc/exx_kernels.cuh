@@ -68,8 +68,6 @@ template <int L1, int L2> struct Scr {
   static constexpr int line = (L2 * row) | 1;
 };
 
-template <typename R> __device__ __forceinline__ R sq(R a) { return a * a; }
-
 // Load of data that other CTAs of the same launch may have written (COH, the
 // persistent batched kernel: through L2, never a stale L1 or read-only-cache
 // line); plain load otherwise.
@@ -554,8 +552,12 @@ __device__ __forceinline__ void zconv_unit(cplx<R>* __restrict__ X, const R* __r
       if constexpr (STAGE) gv = valid ? gsm[kz * W + lane] : R(0);  // lane < W
       else if constexpr (PF) gv = gp[k2];
       else gv = valid ? __ldg(Gk + kz * GR) : R(0);
-      es += gv * (sq(v[k2].x) + sq(v[k2].y));
-      v[k2] = cscale(v[k2], gv);
+      // Ghat |rho_hat|^2 as (Ghat x) x + (Ghat y) y: the products are the
+      // multiplied spectrum itself (two multiplies and two fused adds a point)
+      const C g = cscale(v[k2], gv);
+      es = fma(g.x, v[k2].x, es);
+      es = fma(g.y, v[k2].y, es);
+      v[k2] = g;
     }
     eacc += (double)es;
     if constexpr (!ENERGY_ONLY) {
