@@ -326,16 +326,38 @@ __device__ __forceinline__ void fwd_xy_unit(const R* __restrict__ psi0,
 #pragma unroll
         for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul(v[k1], TWR ? twr[TWR ? k1 : 0] : ty[k1 * L2 + cl16]);
       }
-      for (int n2 = cl16 + 16; n2 < L2; n2 += 16) {  // L2 > 16: further units
-        if (rv) {
-          C v[L1];
+      if constexpr (!PER && L2 > 16 && L2 <= 24) {
+        // L2 > 16 (n = 160): the units n2 = 16 .. L2-1 as half units, lanes 2u
+        // and 2u + 1 of the half warp taking the even and odd outputs of unit
+        // 16 + u (the two length-L1/2 DFTs of the pruned transform), so that
+        // the second round costs half a unit (fwd_xy -5% at 160^3); the same
+        // operations as dft_halfin, so the same results
+        if (rv && cl16 < 2 * (L2 - 16)) {
+          const int n2 = 16 + (cl16 >> 1), hh = cl16 & 1;
+          C e[H1];
 #pragma unroll
-          for (int n1 = 0; n1 < NIN; ++n1) v[n1] = hp[n1 / NB][rb + L2 * (n1 % NB) + n2];
-          dft_fwd_in<L1, PER>(v);
+          for (int n1 = 0; n1 < H1; ++n1) e[n1] = hp[n1 / NB][rb + L2 * (n1 % NB) + n2];
+          if (hh) sfor<H1>([&](auto J) { e[J] = twmul<-1, L1, (int)J>(e[J]); });
+          dft<H1, 1, -1>(e);
           C* o = Sw + n2 * Scr<L1, L2>::row;
-          o[0] = v[0];
 #pragma unroll
-          for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul(v[k1], ty[k1 * L2 + n2]);
+          for (int k = 0; k < H1; ++k) {
+            const int k1 = 2 * k + hh;
+            o[k1] = k1 == 0 ? e[0] : cmul(e[k], ty[k1 * L2 + n2]);
+          }
+        }
+      } else {
+        for (int n2 = cl16 + 16; n2 < L2; n2 += 16) {  // L2 > 16: further units
+          if (rv) {
+            C v[L1];
+#pragma unroll
+            for (int n1 = 0; n1 < NIN; ++n1) v[n1] = hp[n1 / NB][rb + L2 * (n1 % NB) + n2];
+            dft_fwd_in<L1, PER>(v);
+            C* o = Sw + n2 * Scr<L1, L2>::row;
+            o[0] = v[0];
+#pragma unroll
+            for (int k1 = 1; k1 < L1; ++k1) o[k1] = cmul(v[k1], ty[k1 * L2 + n2]);
+          }
         }
       }
       __syncwarp();
