@@ -71,3 +71,42 @@ def test_pair_sample_decode_and_cpu_model():
     for i, j, g in bench.sample_pairs(N, 50, seed=3):
         assert order[g] == (i, j)
     assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
+
+
+def _run_bench(args, env_extra=None):
+    import subprocess
+    import sys
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py")] + args,
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return r.stdout
+
+
+def test_reference_arm_prints_the_contract_line():
+    # the reference arm (the FP64 oracle on the host cores) on the 64-orbital
+    # 96^3 workload: one JSON line with the base contract's keys, the oracle
+    # described as the CPU baseline, and an e2e record without copies
+    out = _run_bench(["--impl", "reference", "--workload", "c2_fp32_n96_N64",
+                      "--steps", "1", "--warmup", "0"])
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["config"]["workload"] == "c2_fp32_n96_N64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    # one step is a measured sample of pair solves; the full-workload time is
+    # a separate, labelled extrapolation
+    assert "measured" in d["ms_per_step_is"]
+    assert d["ms_per_full_workload_extrapolated"] > d["ms_per_step"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    # under torchrun only rank 0 runs the oracle and prints
+    out = _run_bench(["--impl", "reference", "--workload", "c2_fp32_n96_N64", "--steps", "1",
+                      "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert out.strip() == ""
