@@ -253,6 +253,8 @@ struct exx_plan_s {
   double* vacc = nullptr;
   double* E_dev = nullptr;
   int* d_err = nullptr;    // set by a device-side wait that ran out
+  int fail_alloc = 0;      // test hook: this device allocation (1-based) reports out of memory
+  int nalloc = 0;          // device allocations made by dalloc so far
   CUtensorMap gmap{};      // TMA descriptor of the kernel table (Ops::stage_table)
   void* h_psi = nullptr;  // exx_apply_host staging (allocated on first use)
   void* h_vx = nullptr;
@@ -342,6 +344,10 @@ struct ProfScope {
 };
 
 template <typename T> exx_status_t dalloc(exx_plan_t p, T** out, size_t bytes) {
+  if (p->fail_alloc > 0 && ++p->nalloc == p->fail_alloc) {
+    p->err = "simulated allocation failure (EXX_TEST_FAIL_ALLOC)";
+    return EXX_ERR_OOM;
+  }
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
   if (e != cudaSuccess) {
@@ -538,6 +544,13 @@ static exx_status_t plan_create_impl(exx_plan_t* out, const int grid[3], const d
   const long long n3 = (long long)n * n * n;
   const size_t nper = m * (size_t)ops->nyb;
   exx_status_t st_;
+  // test hook (EXX_TEST_FAIL_ALLOC=k, k >= 1): the plan's k-th device
+  // allocation reports out of memory without calling cudaMalloc, so that the
+  // clean-up of a failed creation is tested without exhausting the device
+  {
+    const char* hook = std::getenv("EXX_TEST_FAIL_ALLOC");
+    if (hook != nullptr) p->fail_alloc = std::atoi(hook);
+  }
 #define EXX_ALLOC(ptr, bytes)                 \
   if ((st_ = dalloc(p, &(ptr), (bytes))) != EXX_OK) { \
     free_plan(p);                             \

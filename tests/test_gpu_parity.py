@@ -486,6 +486,33 @@ def test_bounded_wait_times_out_and_context_survives(torch_dev, monkeypatch):
     assert abs(E - Eo) <= 1e-6 and abs(Ee - Eo) <= 1e-6
 
 
+def test_simulated_allocation_failure_returns_oom_and_frees(torch_dev, monkeypatch):
+    # a plan creation whose k-th device allocation fails returns EXX_ERR_OOM,
+    # frees what it had allocated and leaves the context usable; the failure
+    # comes from a host-side test hook (EXX_TEST_FAIL_ALLOC=k), so nothing is
+    # exhausted on the device.  An FP64 plan of 8 orbitals on 64^3 makes ten
+    # allocations (one tile, one lane; the pair spectra alone 306 MB, so a
+    # leak shows in the device's free memory): the first, middle ones, the
+    # spectra (7) and the last fail.
+    torch, dev = torch_dev
+    from paper_1712_07973_gb300 import exx
+    occ8 = np.full(8, 2.0)
+    exx.ExxPlan(64, 0.4, 0.25, occ8, precision="fp64").close()  # context and modules loaded
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 2, 5, 7, 8, 10):
+        monkeypatch.setenv("EXX_TEST_FAIL_ALLOC", str(k))
+        with pytest.raises(exx.ExxError) as ei:
+            exx.ExxPlan(64, 0.4, 0.25, occ8, precision="fp64")
+        assert ei.value.status == 3 and "EXX_ERR_OOM" in str(ei.value), (k, str(ei.value))
+    monkeypatch.delenv("EXX_TEST_FAIL_ALLOC")
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) <= (8 << 20)
+    psi = _orbitals(16, 3, seed=9)
+    occ = np.array([2.0, 1.0, 0.5])
+    _assert_fp64(_gpu(torch_dev, psi, occ, 0.25, 0.45, "fp64"), _oracle(psi, occ, 0.25, 0.45))
+
+
 @pytest.mark.parametrize("n", [112, 128])
 def test_fp64_two_cta_slabs_320_threads(torch_dev, n):
     # FP64 slabs of n = 112 and 128 only fit as two-CTA clusters of 320 threads
